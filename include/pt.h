@@ -1,0 +1,169 @@
+/*
+ * pt.h -- C-ABI of the GB300 parallel-tempering engine for the elastic bead-spring
+ * homopolymer of Gross, Janke and Bachmann ("Massively parallelized replica-exchange
+ * simulations of polymers on GPUs").
+ *
+ * Model (Sec. 3.1): N beads in 3D; every pair i != j interacts through the truncated and
+ * shifted Lennard-Jones potential of Eqs. 1-2 (epsilon = 1, r0 = 0.7, sigma = 2^(-1/6) r0,
+ * rc = 2.5 sigma); consecutive beads are bonded by the FENE potential of Eq. 3 (K = 40,
+ * R = 0.3); the total energy is Eq. 4.
+ * Method: single-bead displacement Metropolis moves (Sec. 3.2, Eq. 5) for every replica,
+ * and neighbour temperature exchanges (Sec. 3.3, Eq. 6) that permute temperature labels.
+ *
+ * Conventions shared by every entry point:
+ *   - All pointers named out/in are HOST memory owned by the caller; the library copies.
+ *     Device memory is owned by the library and released by pt_destroy.
+ *   - Return codes are the pt_status values; on failure pt_last_error() holds a message
+ *     (thread-local, valid until the next failing call on the same thread).
+ *   - Work is enqueued on the context's CUDA stream; pt_sweep returns before the work
+ *     ends. Every call that returns data synchronises that stream first.
+ *   - After PT_ECUDA or PT_ESTATE a context is poisoned: every call but pt_destroy returns
+ *     the same code.
+ *   - Temperature slot t is position t of the temperature array; "replica" r is a
+ *     conformation (storage index). rep_of_temp[t] names the replica at slot t.
+ *   - A context may hold several independent ensembles (pt_create_batch). Per-replica and
+ *     per-slot arrays are then the ensembles' arrays concatenated in ensemble order.
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pt_ctx pt_ctx;
+
+typedef enum pt_status {
+    PT_OK = 0,
+    PT_EINVAL = -1,   /* bad argument or size mismatch; nothing was changed        */
+    PT_ENOMEM = -2,   /* device or host allocation failed                          */
+    PT_ECUDA = -3,    /* a CUDA call or kernel failed; context poisoned            */
+    PT_ESTATE = -4,   /* non-finite energy or broken bond found; context poisoned  */
+    PT_ETIMEOUT = -5, /* a bounded device wait gave up                             */
+    PT_EBUSY = -6     /* resource busy (server full, job not finished)             */
+} pt_status;
+
+/* Parameters of one ensemble. pt_params_init fills the defaults listed here. */
+typedef struct pt_params {
+    int32_t N;                   /* beads per chain, 2 <= N <= PT_MAX_N                     */
+    int32_t n_replicas;          /* replicas = temperature slots, 1 <= n_replicas           */
+    const double* temperatures;  /* host [n_replicas], finite and > 0 (k_B = 1, LJ units)   */
+    uint64_t seed;               /* key of the counter-based random stream                  */
+    uint32_t ensemble_id;        /* < 2^24, part of every counter (default 0)               */
+    float delta;                 /* half-width of the uniform displacement cube (0.3)       */
+    int32_t lj_bonded;           /* 1: LJ also between bonded beads, Eq. 4 as printed (1)   */
+    int32_t n_bins;              /* energy-histogram bins per temperature slot (4096)       */
+    double e_min, e_max;         /* histogram range [e_min, e_max) (-8N, 2N)                */
+    int64_t recompute_every;     /* sweeps between FP64 full-energy recomputes, 0=off (1000)*/
+    int64_t n_therm;             /* sweeps before measurements start (0)                    */
+    const float* init_positions; /* host [n_replicas][N][3], or NULL for a random coil      */
+} pt_params;
+
+#define PT_MAX_N 8192
+
+/* Fill *p with the defaults above for N beads, n_replicas slots, temperatures, seed. */
+void pt_params_init(pt_params* p, int N, int n_replicas, const double* temperatures,
+                    uint64_t seed);
+
+/* ---- the core calls --------------------------------------------------------------- */
+
+/* One ensemble with default parameters (Sec. 3). Returns NULL on error (see
+ * pt_last_error). The start conformations are random-walk coils with all bonds at r0. */
+pt_ctx* pt_create(int N, int n_replicas, const double* temperatures, uint64_t seed);
+
+/* Advance every ensemble of h by n_sweeps sweeps. A sweep is N single-bead moves per
+ * replica (Sec. 3.2); after the moves of sweep s (0-based, counted since creation) the
+ * energies are measured and, if exchange_every > 0 and (s + 1) % exchange_every == 0,
+ * one exchange round (Sec. 3.3, Eq. 6) permutes the temperature labels. Asynchronous. */
+int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every);
+
+/* Tracked energy (FP64) of the replica at each temperature slot; n == total slots. */
+int pt_energies(pt_ctx* h, double* out, int n);
+
+/* Energy histograms, one row of n_bins FP64 counts per temperature slot; n == sum of
+ * slots x n_bins. Bin b of slot t counts measurements with
+ * floor((E - e_min) * (n_bins / (e_max - e_min))) == b. */
+int pt_histograms(pt_ctx* h, double* out, int64_t n);
+
+/* Release everything; NULL is allowed. */
+void pt_destroy(pt_ctx* h);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* pt_last_error(void);
+
+/* ---- extensions (same conventions) ----------------------------------------------- */
+
+/* One ensemble with explicit parameters; stream is a cudaStream_t (NULL: the library
+ * makes its own non-blocking stream). */
+pt_ctx* pt_create_ex(const pt_params* p, void* stream);
+
+/* Several independent ensembles advanced together by one set of launches. */
+pt_ctx* pt_create_batch(int n_ensembles, const pt_params* params, void* stream);
+
+/* Use another CUDA stream from now on (waits for the old one first). */
+int pt_set_stream(pt_ctx* h, void* stream);
+
+/* Block until all work enqueued on h has finished; reports device-side errors. */
+int pt_sync(pt_ctx* h);
+
+/* Shape queries: number of ensembles; total slots; for ensemble e its N, slots, bins. */
+int pt_num_ensembles(const pt_ctx* h);
+int pt_total_replicas(const pt_ctx* h);
+int pt_ensemble_shape(const pt_ctx* h, int e, int* N, int* n_replicas, int* n_bins);
+
+/* Conformations [replica][N][3] as float (n == sum of replicas x N x 3). Setting them
+ * recomputes every tracked energy in FP64 (Eq. 4) and checks all bonds. */
+int pt_get_positions(pt_ctx* h, float* out, int64_t n);
+int pt_set_positions(pt_ctx* h, const float* in, int64_t n);
+
+/* Replica at each temperature slot (n == total slots). */
+int pt_get_permutation(pt_ctx* h, int32_t* rep_of_temp, int n);
+
+/* Per temperature slot: count, sum E, sum E^2 (FP64), the inputs of Eq. 7; n == 3 x slots. */
+int pt_moments(pt_ctx* h, double* out, int64_t n);
+
+/* Per temperature slot: measurements below e_min and at or above e_max; n == 2 x slots. */
+int pt_hist_outliers(pt_ctx* h, double* out, int64_t n);
+
+/* Move attempts / acceptances per temperature slot (n == slots each) and exchange
+ * attempts / acceptances per slot pair (t, t+1) (n == slots each; the last entry of every
+ * ensemble is 0). Any pointer may be NULL. */
+int pt_acceptance(pt_ctx* h, uint64_t* move_att, uint64_t* move_acc, uint64_t* ex_att,
+                  uint64_t* ex_acc, int n);
+
+/* Largest |E_tracked - E_FP64| seen at the periodic recomputes, per replica (n == slots). */
+int pt_drift(pt_ctx* h, double* out, int n);
+
+/* Sweeps done by ensemble e, exchange rounds done by ensemble e. */
+int pt_counters(pt_ctx* h, int e, int64_t* sweeps, int64_t* exchange_rounds);
+
+/* Record every move of sweeps [first_sweep, first_sweep + n_sweeps) (0 disables). */
+int pt_set_debug_log(pt_ctx* h, int64_t first_sweep, int64_t n_sweeps);
+
+/* Copy the log. Per logged sweep s and replica r (row offset = sum of N of the replicas
+ * before r): bead [s][row + m], dE (FP32 value used by the decision), theta (FP32
+ * Metropolis threshold), acc (0/1). e_after [s][replica]: tracked energy after the moves
+ * (and recompute). xchg [s][slot]: -1 no attempt, 0 rejected, 1 swapped (pair t, t+1).
+ * Any pointer may be NULL; sizes follow from the shape and the window. */
+int pt_get_debug_log(pt_ctx* h, int32_t* bead, float* de, float* theta, uint8_t* acc,
+                     double* e_after, int8_t* xchg);
+
+/* FP64 total energy (Eq. 4) of n_conf conformations of N beads, host in [n][N][3],
+ * host out [n]. Uses the context's stream and device scratch. */
+int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonded,
+                   double* out);
+
+/* Checkpoint of the whole state (positions, energies, labels, counters, histograms,
+ * moments, acceptance). With buf == NULL only *size is set. pt_restore needs a context
+ * created with the same shapes and parameters. The random stream is counter-based, so a
+ * restored run continues bit-identically. */
+int pt_checkpoint(pt_ctx* h, void* buf, size_t* size);
+int pt_restore(pt_ctx* h, const void* buf, size_t size);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PT_H */

@@ -1,0 +1,302 @@
+"""Benchmark: single-bead Metropolis updates per second of the parallel-tempering engine.
+
+Workload (one GPU): 4 independent PT ensembles (seeds 1-4) of an N = 100 bead chain with
+64 replicas at geometric temperatures 0.2-3.0, displacement half-width 0.3, an exchange
+round after every sweep, an FP64 full-energy recompute every 1000 sweeps and 4096 FP64
+histogram bins per temperature slot. One step = 1000 sweeps of all four ensembles
+(4 x 64 x 100 x 1000 = 25.6 M single-bead updates); 100 steps are the whole 1e5-sweep run.
+Under torchrun every rank runs its own four ensembles (seeds 4 rank + 1 ... 4 rank + 4):
+weak scaling, no collective on the data path.
+
+Prints one JSON line (see the repository's benchmark contract). ``--impl reference`` times
+the FP64 CPU oracle instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_BEADS, N_REP, N_ENS, T_MIN, T_MAX = 100, 64, 4, 0.2, 3.0
+SWEEPS_PER_STEP = 1000
+FLOPS_PER_PAIR = 15  # FP32 flops per pair evaluation (FMA = 2), see the design notes
+METRIC = "single-bead Metropolis updates/sec (all replicas)"
+UNIT = "updates/s"
+WORKLOAD = (f"PT polymer N={N_BEADS} beads, {N_REP} replicas at T geometric {T_MIN}-{T_MAX}, "
+            f"{N_ENS} ensembles (seeds 1-{N_ENS}) per GPU, delta 0.3, exchange every sweep, "
+            f"FP64 recompute every 1000 sweeps, 4096 FP64 bins/slot; 1 step = {SWEEPS_PER_STEP} sweeps")
+
+
+def updates_per_step(n_ens=N_ENS):
+    return n_ens * N_REP * N_BEADS * SWEEPS_PER_STEP
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws: int, backend: str):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def reduce_max(value: float, dist, device=None) -> float:
+    """Max over ranks of a host scalar (no data-path collective: timing only)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def ensemble_params(rank: int):
+    from paper_1107_3490_gb300 import inputs, pt
+    made = []
+    for e in range(N_ENS):
+        seed = N_ENS * rank + e + 1
+        T = inputs.temperature_ladder(T_MIN, T_MAX, N_REP)
+        x0 = inputs.random_coil(N_BEADS, N_REP, seed, seed - 1)
+        made.append(pt.make_params(N_BEADS, T, seed, ensemble_id=seed - 1, init_positions=x0,
+                                   delta=0.3, recompute_every=1000, n_bins=4096))
+    return made
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.file is None:
+            return None
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
+    """FP32 peak: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return num_sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def cpu_baseline(target_s: float = 15.0, threads: int | None = None):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload:
+    ensemble seed 1 (N = 100, 64 replicas), exchange every sweep."""
+    import oracle
+    from paper_1107_3490_gb300 import inputs
+    threads = threads or os.cpu_count() or 1
+    T = inputs.temperature_ladder(T_MIN, T_MAX, N_REP)
+    ens = oracle.OracleEnsemble(inputs.random_coil(N_BEADS, N_REP, 1, 0), T, 1, delta=0.3,
+                                recompute_every=1000, n_bins=4096, threads=threads)
+    t0 = time.perf_counter()
+    ens.run(2, 1)
+    per_sweep = (time.perf_counter() - t0) / 2
+    n = max(2, int(target_s / max(per_sweep, 1e-6)))
+    t0 = time.perf_counter()
+    ens.run(n, 1)
+    dt = time.perf_counter() - t0
+    return {"value": N_REP * N_BEADS * n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"ensemble seed 1 of {N_ENS} (N={N_BEADS}, {N_REP} replicas), {n} sweeps after 2 warm-up "
+                      f"sweeps, exchange every sweep, FP64 oracle with {threads} OpenMP threads; {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    import oracle
+    from paper_1107_3490_gb300 import inputs
+    threads = os.cpu_count() or 1
+    T = inputs.temperature_ladder(T_MIN, T_MAX, N_REP)
+    ens = oracle.OracleEnsemble(inputs.random_coil(N_BEADS, N_REP, 1, 0), T, 1, delta=0.3,
+                                recompute_every=1000, n_bins=4096, threads=threads)
+    t0 = time.perf_counter()
+    ens.run(2, 1)
+    per_sweep = (time.perf_counter() - t0) / 2
+    budget = 150.0 / max(1, args.steps + args.warmup)  # whole run within a few minutes
+    sweeps = max(1, int(budget / max(per_sweep, 1e-6)))
+    for _ in range(args.warmup):
+        ens.run(sweeps, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ens.run(sweeps, 1)
+        times.append(time.perf_counter() - t0)
+    upd = N_REP * N_BEADS * sweeps
+    value = upd * len(times) / sum(times)
+    sample = (f"each step: {sweeps} sweeps of ensemble seed 1 (N={N_BEADS}, {N_REP} replicas), "
+              f"exchange every sweep, FP64 oracle, {threads} OpenMP threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "reference_sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(ws, "nccl")
+    from paper_1107_3490_gb300 import pt
+
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.Stream(device=dev)
+    made = ensemble_params(rank)
+    h = pt.pt_create_batch([p for p, _ in made], stream.cuda_stream)
+    pt.pt_set_kernel_timing(h, True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB of L2
+
+    for _ in range(args.warmup):
+        pt.pt_sweep(h, SWEEPS_PER_STEP, 1)
+    pt.pt_sync(h)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            starts[k].record(stream)
+            pt.pt_sweep(h, SWEEPS_PER_STEP, 1)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kernel_ms, kernel_n = pt.pt_kernel_timing(h)
+    pt.pt_sync(h)
+    local_ms = sum(step_ms)
+    total_ms = reduce_max(local_ms, dist, dev)
+    value = updates_per_step() * ws * args.steps / (total_ms / 1e3)
+    clocks = clk.summary()
+
+    # ---- end to end through the C-ABI with host buffers: restore the state from pinned host
+    # memory, run the step, checkpoint it back to pinned host memory
+    nbytes = pt.pt_checkpoint_size(h)
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    pt.pt_checkpoint_into(h, host)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pt.pt_restore_from(h, host, nbytes)
+        pt.pt_sweep(h, SWEEPS_PER_STEP, 1)
+        pt.pt_checkpoint_into(h, host)
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": updates_per_step() * ws * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # ---- roofline of the dominant kernel (the sweep): plain FP32 ALU work
+    pairs_per_launch = N_ENS * N_REP * N_BEADS * 2 * (N_BEADS - 1)  # one sweep per launch
+    achieved = pairs_per_launch * FLOPS_PER_PAIR / (kernel_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops(num_sms, 2070.0)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_sweep", "launch_ms": kernel_ms, "launches_sampled": kernel_n,
+                "peak_basis": f"{num_sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)"}
+    if clocks and clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / fp32_peak_tflops(num_sms, clocks["sm_mhz"])
+    pt.pt_destroy(h)
+
+    launches_per_step = 1 + -(-SWEEPS_PER_STEP // 32) * 64
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": f"ensembles per GPU, {ws} GPU(s), no collective",
+                       "l2": "256 MB buffer written between timed steps (outside the per-step events)",
+                       "pair_evals_per_s": value * 2 * (N_BEADS - 1)},
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
+            "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    from paper_1107_3490_gb300 import build
+    build.build()
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

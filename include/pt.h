@@ -106,6 +106,9 @@ pt_ctx* pt_create_batch(int n_ensembles, const pt_params* params, void* stream);
 /* Use another CUDA stream from now on (waits for the old one first). */
 int pt_set_stream(pt_ctx* h, void* stream);
 
+/* The cudaStream_t the context enqueues on (for events and ordering by the caller). */
+void* pt_get_stream(pt_ctx* h);
+
 /* Block until all work enqueued on h has finished; reports device-side errors. */
 int pt_sync(pt_ctx* h);
 
@@ -155,6 +158,13 @@ int pt_get_debug_log(pt_ctx* h, int32_t* bead, float* de, float* theta, uint8_t*
  * host out [n]. Uses the context's stream and device scratch. */
 int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonded,
                    double* out);
+
+/* Kernel timing for profiling: with on = 1 every sweep-kernel launch is bracketed by CUDA
+ * events on the context's stream (inside the captured graph too). pt_kernel_timing then
+ * reports the mean duration of the sweep launches of the most recent graph replay (or of
+ * the last <= 64 direct launches) and how many launches that mean covers. */
+int pt_set_kernel_timing(pt_ctx* h, int on);
+int pt_kernel_timing(pt_ctx* h, double* mean_sweep_ms, int* n_launches);
 
 /* Checkpoint of the whole state (positions, energies, labels, counters, histograms,
  * moments, acceptance). With buf == NULL only *size is set. pt_restore needs a context

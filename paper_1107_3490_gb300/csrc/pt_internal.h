@@ -1,0 +1,79 @@
+// pt_internal.h -- device-state layout shared by the host runtime and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ptgb {
+
+// One replica (conformation). Global replica index g = rep_base(ensemble) + r.
+struct RepDev {
+    int32_t ens;        // ensemble index
+    int32_t r;          // replica index inside the ensemble (keys the random stream)
+    int32_t N;          // beads
+    int32_t pos_off;    // offset of bead 0 in the position array (float4 units)
+    int32_t slot_base;  // global index of temperature slot 0 of its ensemble
+    int32_t pad[3];
+};
+
+// One ensemble. The first block is written at creation; target / exchange_every by every
+// pt_sweep; xround / last_x_sweep only by the exchange kernel.
+struct EnsDev {
+    uint64_t seed;
+    uint32_t ens_id;
+    float delta;
+    int32_t lj_bonded, N, R, rep_base;
+    int32_t n_bins, exchange_every;
+    int64_t hist_base;
+    double e_min, inv_w;  // inv_w = n_bins / (e_max - e_min)
+    int64_t recompute_every, n_therm;
+    int64_t target;        // the sweep kernels stop every replica of the ensemble here
+    int64_t xround;        // exchange rounds done
+    int64_t last_x_sweep;  // sweep count at the last exchange (guards repeated launches)
+};
+
+// Error bits raised by kernels.
+enum : int { kErrNonFinite = 1, kErrTimeout = 2 };
+
+struct State {
+    RepDev* reps;
+    EnsDev* ens;
+    int n_reps, n_ens, nmax;  // nmax = largest N
+    float4* pos;              // [sum N] xyz + unused w
+    double* E;                // [replica]
+    int32_t* temp_of_rep;     // [replica] local slot
+    int32_t* rep_of_temp;     // [slot] local replica
+    float* Tf;                // [slot] temperature, float (Metropolis threshold)
+    double* beta;             // [slot] 1/T, double (exchange)
+    double* hist;             // [sum R n_bins]
+    double* outl;             // [slot][2]
+    double* mom;              // [slot][3]
+    unsigned long long *mv_att, *mv_acc, *ex_att, *ex_acc;  // [slot]
+    double* drift;            // [replica]
+    int64_t* rep_sweep;       // [replica] sweeps done
+    int* err;                 // error bits
+    // per-move log of sweeps [log_s0, log_s0 + log_ns); null pointers when off
+    int64_t log_s0, log_ns, log_pstride;  // log_pstride = total positions
+    int32_t* log_bead;
+    float* log_de;
+    float* log_theta;
+    uint8_t* log_acc;
+    double* log_e;   // [s][replica]
+    int8_t* log_x;   // [s][slot]
+};
+
+// Launchers (pt_kernels.cu). All are asynchronous on `st`.
+int sweep_warps_per_block(int nmax, int n_reps, int num_sms);
+size_t sweep_smem_bytes(int nmax, int warps);
+cudaError_t configure_sweep(int nmax, int warps);  // once per context, before any capture
+cudaError_t launch_sweep(const State& s, int chunk, int warps, cudaStream_t st);
+cudaError_t launch_exchange(const State& s, cudaStream_t st);
+
+// FP64 total energy (Eq. 4) of n_conf conformations. Conformation c has N_c beads at
+// pos[off_c ...]; with reps == nullptr every conformation has N beads at pos[c * N].
+// scratch holds n_conf * n_chunks doubles.
+__host__ __device__ int energy_chunks(int N);
+cudaError_t launch_energy(const float4* pos, const RepDev* reps, const EnsDev* ens, int N,
+                          int lj_bonded, int n_conf, double* out, double* scratch, int n_chunks,
+                          cudaStream_t st);
+
+}  // namespace ptgb

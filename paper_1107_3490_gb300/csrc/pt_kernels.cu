@@ -1,0 +1,338 @@
+// pt_kernels.cu -- sweep, exchange and FP64 energy kernels of the PT engine.
+//
+// Sweep (Sec. 3.2): one warp owns one replica. Its chain sits in shared memory as float4
+// for the whole launch. A move is: the Philox draws (computed 32 moves at a time, one move
+// per lane, then broadcast), the proposal rounded to float, the O(N) energy row of the
+// moved bead spread over the 32 lanes (FP32 for ordinary pairs; steep pairs and the two
+// FENE bonds queued and re-evaluated in double-float), a butterfly reduction that leaves
+// the same sum in every lane, and the Metropolis decision dE < theta (Eq. 5) with
+// theta = -log(u) T formed in float. Accepted dE are summed in double-float and added to
+// the FP64 energy at the end of the sweep; then the periodic FP64 recompute (Eq. 4), the
+// measurement into the temperature slot's histogram and moments, and the counters.
+// Exchange (Sec. 3.3, Eq. 6): one warp per ensemble runs one even/odd round on the labels.
+#include <cfloat>
+#include <cmath>
+
+#include "pt_device.cuh"
+#include "pt_internal.h"
+
+namespace ptgb {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int m = 16; m; m >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, m));
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+    return v;
+}
+
+// FP64 total energy of the chain in shared memory, computed by one warp (Eq. 4).
+__device__ double warp_full_energy(const float4* P, int N, int lj_bonded, int lane) {
+    double e = 0.0;
+    for (int i = lane; i < N; i += 32) {
+        float4 pi = P[i];
+        for (int j = i + 1; j < N; ++j) {
+            double r2 = r2_d(pi, P[j]);
+            if (j == i + 1) {
+                e += fene_d(r2);
+                if (lj_bonded) e += lj_mod_d(r2);
+            } else {
+                e += lj_mod_d(r2);
+            }
+        }
+    }
+    return warp_sum_d(e);
+}
+
+__global__ void __launch_bounds__(128) k_sweep(State S, int chunk) {
+    extern __shared__ float4 smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (g >= S.n_reps) return;  // whole warp leaves; no block-wide barrier is used
+    const RepDev rd = S.reps[g];
+    const EnsDev ed = S.ens[rd.ens];
+    const int N = rd.N;
+    float4* P = smem + (size_t)warp * (S.nmax + (S.nmax + 3) / 4);
+    int* queue = reinterpret_cast<int*>(P + S.nmax);
+
+    int64_t s = S.rep_sweep[g];
+    const int64_t s_end = min(ed.target, s + (int64_t)chunk);
+    if (s >= s_end) return;
+
+    for (int i = lane; i < N; i += 32) P[i] = S.pos[rd.pos_off + i];
+    __syncwarp();
+
+    double E = S.E[g];
+    const int slot = S.temp_of_rep[g];
+    const int gs = rd.slot_base + slot;
+    const float Tf = S.Tf[gs];
+    const uint32_t k0 = (uint32_t)ed.seed, k1 = (uint32_t)(ed.seed >> 32);
+    const uint32_t c3 = ed.ens_id | (kTagMove << 24);
+    const bool ljb = ed.lj_bonded != 0;
+    const float delta = ed.delta;
+
+    for (; s < s_end; ++s) {
+        const bool logging = S.log_bead && s >= S.log_s0 && s < S.log_s0 + S.log_ns;
+        const size_t lrow = logging ? (size_t)(s - S.log_s0) * S.log_pstride + rd.pos_off : 0;
+        df dsum = {0.f, 0.f};
+        int nacc = 0;
+        for (int m0 = 0; m0 < N; m0 += 32) {
+            // draws of move m0 + lane (Sec. 3.2): bead, displacement, threshold
+            int km = 0;
+            float sx = 0.f, sy = 0.f, sz = 0.f, th = 0.f;
+            if (m0 + lane < N) {
+                const uint32_t m = (uint32_t)(m0 + lane);
+                u4 w = philox(u4{2u * m, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                u4 v = philox(u4{2u * m + 1u, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                km = (int)__umulhi(w.x, (uint32_t)N);
+                sx = __fsub_rn(__fmul_rn(2.f, unif24(w.y)), 1.f);
+                sy = __fsub_rn(__fmul_rn(2.f, unif24(w.z)), 1.f);
+                sz = __fsub_rn(__fmul_rn(2.f, unif24(w.w)), 1.f);
+                th = __fmul_rn(-logf(unif24(v.x)), Tf);
+            }
+            const int mc = min(32, N - m0);
+            for (int i = 0; i < mc; ++i) {
+                const int k = __shfl_sync(kFull, km, i);
+                const float ux = __shfl_sync(kFull, sx, i), uy = __shfl_sync(kFull, sy, i),
+                            uz = __shfl_sync(kFull, sz, i), theta = __shfl_sync(kFull, th, i);
+                const float4 p4 = P[k];
+                const float3 p = make_float3(p4.x, p4.y, p4.z);
+                const float3 pn = make_float3(__fadd_rn(p.x, __fmul_rn(delta, ux)),
+                                              __fadd_rn(p.y, __fmul_rn(delta, uy)),
+                                              __fadd_rn(p.z, __fmul_rn(delta, uz)));
+                // ---- FP32 row over ordinary partners; steep ones go to the queue
+                float acc = 0.f;
+                int qn = 0;
+                for (int j0 = 0; j0 < N; j0 += 32) {
+                    const int j = j0 + lane;
+                    const float4 q = P[min(j, N - 1)];
+                    // explicit round-to-nearest intrinsics: the old and new sides get the
+                    // same instruction sequence, so an unchanged distance gives equal x
+                    const float dxo = __fsub_rn(q.x, p.x), dyo = __fsub_rn(q.y, p.y), dzo = __fsub_rn(q.z, p.z);
+                    const float dxn = __fsub_rn(q.x, pn.x), dyn = __fsub_rn(q.y, pn.y), dzn = __fsub_rn(q.z, pn.z);
+                    const float r2o = __fmaf_rn(dzo, dzo, __fmaf_rn(dyo, dyo, __fmul_rn(dxo, dxo)));
+                    const float r2n = __fmaf_rn(dzn, dzn, __fmaf_rn(dyn, dyn, __fmul_rn(dxn, dxn)));
+                    const bool ordinary = j < N && (unsigned)(j - k + 1) > 2u;
+                    const bool steep = ordinary && fminf(r2o, r2n) < kSteep2f;
+                    const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
+                    const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
+                    // x (A x - B) at new minus old = (xn - xo)(A (xn + xo) - B): exactly 0 when
+                    // the distance is unchanged (every pair beyond the cutoff, delta = 0)
+                    if (ordinary && !steep)
+                        acc = __fmaf_rn(__fsub_rn(xn, xo), __fmaf_rn(kAf, __fadd_rn(xn, xo), -kBf), acc);
+                    const unsigned bm = __ballot_sync(kFull, steep);
+                    if (steep) queue[qn + __popc(bm & lanemask_lt())] = j;
+                    qn += __popc(bm);
+                }
+                __syncwarp();
+                // ---- bonds (k-1, k), (k, k+1) and the queued steep pairs in double-float
+                const int nb0 = k > 0 ? 1 : 0, nb = nb0 + (k + 1 < N ? 1 : 0);
+                bool broken = false;
+                for (int i2 = lane; i2 < nb + qn; i2 += 32) {
+                    const bool bonded = i2 < nb;
+                    const int j = bonded ? ((i2 == 0 && nb0) ? k - 1 : k + 1) : queue[i2 - nb];
+                    acc = __fadd_rn(acc, pair_term_accurate(P[j], p, pn, bonded ? ljb : true, bonded, &broken));
+                }
+                acc = warp_sum(acc);
+                broken = __any_sync(kFull, broken);
+                const float dE = broken ? __int_as_float(0x7f800000) : acc;
+                const bool accept = dE < theta;  // NaN and +inf reject
+                if (accept) {
+                    if (lane == 0) P[k] = make_float4(pn.x, pn.y, pn.z, 0.f);
+                    dsum = df_add(dsum, df{dE, 0.f});
+                    ++nacc;
+                }
+                if (logging && lane == 0) {
+                    const size_t li = lrow + m0 + i;
+                    S.log_bead[li] = k;
+                    S.log_de[li] = dE;
+                    S.log_theta[li] = theta;
+                    S.log_acc[li] = accept ? 1 : 0;
+                }
+                __syncwarp();
+            }
+        }
+        E = (E + (double)dsum.hi) + (double)dsum.lo;
+        // ---- periodic FP64 recompute of Eq. 4
+        if (ed.recompute_every > 0 && (s + 1) % ed.recompute_every == 0) {
+            const double full = warp_full_energy(P, N, ed.lj_bonded, lane);
+            if (lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
+            E = full;
+        }
+        if (lane == 0) {
+            if (!isfinite(E)) {
+                atomicOr(S.err, kErrNonFinite);
+            } else if (s >= ed.n_therm) {
+                // ---- measurement in the replica's temperature slot (it owns the slot
+                // until the next exchange, so plain read-modify-write is race-free)
+                if (E < ed.e_min) {
+                    S.outl[2 * gs] += 1.0;
+                } else {
+                    const double b = floor((E - ed.e_min) * ed.inv_w);
+                    if (b >= (double)ed.n_bins) S.outl[2 * gs + 1] += 1.0;
+                    else S.hist[ed.hist_base + (int64_t)slot * ed.n_bins + (int64_t)b] += 1.0;
+                }
+                S.mom[3 * gs] += 1.0;
+                S.mom[3 * gs + 1] += E;
+                S.mom[3 * gs + 2] += E * E;
+            }
+            S.mv_att[gs] += (unsigned long long)N;
+            S.mv_acc[gs] += (unsigned long long)nacc;
+            if (logging) S.log_e[(size_t)(s - S.log_s0) * S.n_reps + g] = E;
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < N; i += 32) S.pos[rd.pos_off + i] = P[i];
+    if (lane == 0) {
+        S.E[g] = E;
+        S.rep_sweep[g] = s_end;
+    }
+}
+
+// One exchange round per ensemble that is due (Sec. 3.3, Eq. 6). One warp per ensemble;
+// the pairs of a round are disjoint, so lanes swap labels without conflicts.
+__global__ void k_exchange(State S) {
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (e >= S.n_ens) return;
+    EnsDev* ed = S.ens + e;
+    const int base = ed->rep_base, R = ed->R;
+    const int64_t sw = S.rep_sweep[base];
+    const int xe = ed->exchange_every;
+    if (xe <= 0 || R < 2 || sw == 0 || sw % xe != 0 || sw <= ed->last_x_sweep) return;
+    const int64_t x = ed->xround;
+    const int q = (int)(x & 1);
+    const uint32_t k0 = (uint32_t)ed->seed, k1 = (uint32_t)(ed->seed >> 32);
+    const int64_t s_log = sw - 1;
+    int8_t* xo = (S.log_x && s_log >= S.log_s0 && s_log < S.log_s0 + S.log_ns)
+                     ? S.log_x + (size_t)(s_log - S.log_s0) * S.n_reps + base
+                     : nullptr;
+    if (xo)
+        for (int t = lane; t < R; t += 32) xo[t] = -1;
+    __syncwarp();
+    for (int t = q + 2 * lane; t + 1 < R; t += 64) {
+        const int ra = S.rep_of_temp[base + t], rb = S.rep_of_temp[base + t + 1];
+        const double arg = (S.E[base + ra] - S.E[base + rb]) * (S.beta[base + t] - S.beta[base + t + 1]);
+        const u4 w = philox(u4{(uint32_t)t, (uint32_t)x, 0u, ed->ens_id | (kTagExch << 24)}, k0, k1);
+        const double u = (double)(w.x >> 8) * (1.0 / 16777216.0);
+        const bool acc = u < exp(arg);
+        S.ex_att[base + t] += 1ull;
+        if (acc) {
+            S.ex_acc[base + t] += 1ull;
+            S.rep_of_temp[base + t] = rb;
+            S.rep_of_temp[base + t + 1] = ra;
+            S.temp_of_rep[base + rb] = t;
+            S.temp_of_rep[base + ra] = t + 1;
+        }
+        if (xo) xo[t] = acc ? 1 : 0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        ed->xround = x + 1;
+        ed->last_x_sweep = sw;
+    }
+}
+
+// Row chunks per conformation: a function of N alone, so that a conformation's FP64 sum
+// (and its rounding) does not depend on which other conformations share the launch.
+__host__ __device__ int energy_chunks(int N) {
+    int c = N / 8;
+    if (c > 64) c = 64;
+    return c < 1 ? 1 : c;
+}
+
+// ---- FP64 energies of conformations in global memory (two passes through scratch) -----
+__global__ void __launch_bounds__(256) k_energy_partial(const float4* __restrict__ pos, const RepDev* reps,
+                                                        const EnsDev* ens, int N_u, int ljb_u, int n_chunks,
+                                                        double* __restrict__ scratch) {
+    const int c = blockIdx.x, b = blockIdx.y;
+    int N = N_u, ljb = ljb_u;
+    const float4* P = pos + (size_t)c * N_u;
+    if (reps) {
+        N = reps[c].N;
+        P = pos + reps[c].pos_off;
+        ljb = ens[reps[c].ens].lj_bonded;
+    }
+    // this conformation's own chunking (a function of its N only); surplus blocks add 0
+    const int nc = energy_chunks(N);
+    double e = 0.0;
+    for (int i = b; b < nc && i < N; i += nc) {
+        const float4 pi = P[i];
+        for (int j = i + 1 + threadIdx.x; j < N; j += blockDim.x) {
+            const double r2 = r2_d(pi, P[j]);
+            if (j == i + 1) {
+                e += fene_d(r2);
+                if (ljb) e += lj_mod_d(r2);
+            } else {
+                e += lj_mod_d(r2);
+            }
+        }
+    }
+    __shared__ double red[8];
+    e = warp_sum_d(e);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        scratch[(size_t)c * n_chunks + b] = t;
+    }
+}
+
+__global__ void k_energy_final(const double* __restrict__ scratch, int n_conf, int n_chunks, double* out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_conf) return;
+    double t = 0.0;
+    for (int b = 0; b < n_chunks; ++b) t += scratch[(size_t)c * n_chunks + b];
+    out[c] = t;
+}
+
+// ---- launchers ----------------------------------------------------------------------------
+size_t sweep_smem_bytes(int nmax, int warps) {
+    return (size_t)warps * ((size_t)nmax + (size_t)(nmax + 3) / 4) * sizeof(float4);
+}
+
+int sweep_warps_per_block(int nmax, int n_reps, int num_sms) {
+    int w = 4;
+    while (w > 1 && sweep_smem_bytes(nmax, w) > 200 * 1024) w >>= 1;
+    // few replicas: spread them over the SMs instead of packing them
+    while (w > 1 && (n_reps + w - 1) / w < 2 * num_sms) w >>= 1;
+    return w;
+}
+
+cudaError_t configure_sweep(int nmax, int warps) {
+    const size_t smem = sweep_smem_bytes(nmax, warps);
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_sweep(const State& s, int chunk, int warps, cudaStream_t st) {
+    const size_t smem = sweep_smem_bytes(s.nmax, warps);
+    const int blocks = (s.n_reps + warps - 1) / warps;
+    k_sweep<<<blocks, 32 * warps, smem, st>>>(s, chunk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exchange(const State& s, cudaStream_t st) {
+    const int wpb = 4;
+    k_exchange<<<(s.n_ens + wpb - 1) / wpb, 32 * wpb, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+
+cudaError_t launch_energy(const float4* pos, const RepDev* reps, const EnsDev* ens, int N, int lj_bonded,
+                          int n_conf, double* out, double* scratch, int n_chunks, cudaStream_t st) {
+    if (n_conf <= 0) return cudaSuccess;
+    k_energy_partial<<<dim3(n_conf, n_chunks), 256, 0, st>>>(pos, reps, ens, N, lj_bonded, n_chunks, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_energy_final<<<(n_conf + 127) / 128, 128, 0, st>>>(scratch, n_conf, n_chunks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ptgb

@@ -1,0 +1,201 @@
+"""Engine-level GPU tests through the C-ABI: statistics against quadrature and enumeration,
+checkpoint / restore, split runs, batching, and error handling."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import quadrature as Q
+from paper_1107_3490_gb300 import inputs, pt
+
+pytestmark = pytest.mark.gpu
+
+
+def _block_se(x, n_blocks=40):
+    x = np.asarray(x)
+    b = x[: len(x) // n_blocks * n_blocks].reshape(n_blocks, -1).mean(axis=1)
+    return b.std(ddof=1) / math.sqrt(n_blocks)
+
+
+@pytest.mark.parametrize("lj_bonded", [1, 0])
+def test_dimer_mean_energy_matches_quadrature(lj_bonded):
+    T = np.array([0.3, 0.6, 1.0, 3.0])
+    x0 = np.zeros((4, 2, 3), dtype=np.float32)
+    x0[:, 1, 0] = 0.7
+    p, keep = pt.make_params(2, T, 2024, init_positions=x0, lj_bonded=lj_bonded, n_bins=64,
+                             e_min=-2.0, e_max=6.0, recompute_every=0)
+    h = pt.pt_create_ex(p)
+    n = 200000
+    try:
+        pt.pt_sweep(h, 2000, 1)
+        rot0 = pt.pt_get_permutation(h)
+        pt.pt_set_debug_log(h, 2000, n)
+        pt.pt_sweep(h, n, 1)
+        g = pt.pt_get_debug_log(h, n)
+    finally:
+        pt.pt_destroy(h)
+    rot = rot0.copy()
+    per_slot = np.zeros((n, 4))
+    for s in range(n):
+        per_slot[s] = g["e"][s][rot]
+        for t in np.nonzero(g["x"][s] == 1)[0]:
+            rot[t], rot[t + 1] = rot[t + 1], rot[t]
+    for t in range(4):
+        m1 = Q.dimer_moments(T[t], lj_bonded)[0]
+        e = per_slot[:, t]
+        assert abs(e.mean() - m1) < 4 * _block_se(e) + 1e-4, (T[t], e.mean(), m1)
+
+
+def test_exchange_slot_marginals_enumeration():
+    """Frozen conformations (delta = 0): only labels move; slot occupancies from the
+    device histograms against exact enumeration of Eq. 6's stationary law."""
+    T = np.array([0.5, 0.8, 1.3, 2.0])
+    angles = np.deg2rad([60.0, 90.0, 120.0, 180.0])
+    x0 = np.zeros((4, 3, 3), dtype=np.float32)
+    for r, a in enumerate(angles):
+        x0[r, 1] = [0.7, 0, 0]
+        x0[r, 2] = [0.7 - 0.7 * math.cos(a), 0.7 * math.sin(a), 0]
+    n = 400000
+    p, keep = pt.make_params(3, T, 31, init_positions=x0, delta=0.0, n_bins=4096, e_min=-6, e_max=2,
+                             recompute_every=0)
+    h = pt.pt_create_ex(p)
+    try:
+        e = pt.pt_energies(h)
+        pt.pt_sweep(h, n, 1)
+        hist = pt.pt_histograms(h).reshape(4, 4096)
+        e_after = pt.pt_energies(h)
+    finally:
+        pt.pt_destroy(h)
+    assert np.array_equal(np.sort(e_after), np.sort(e))
+    M = Q.exchange_slot_marginals(e, T)
+    bins = np.floor((e + 6.0) * (4096 / 8.0)).astype(int)
+    assert len(set(bins)) == 4
+    for t in range(4):
+        counts = hist[t, bins]
+        assert counts.sum() == n
+        expect = M[t] * n
+        sd = np.sqrt(expect * (1 - M[t]) * 20) + 1
+        assert np.all(np.abs(counts - expect) < 5 * sd), (t, counts, expect)
+
+
+def _make(N=30, R=8, seed=3, **kw):
+    T = inputs.temperature_ladder(0.3, 3.0, R)
+    x0 = inputs.random_coil(N, R, seed)
+    p, keep = pt.make_params(N, T, seed, init_positions=x0, **kw)
+    return pt.pt_create_ex(p)
+
+
+def _state(h):
+    return (pt.pt_get_positions(h), pt.pt_energies(h), pt.pt_get_permutation(h), pt.pt_histograms(h),
+            pt.pt_moments(h), pt.pt_acceptance(h))
+
+
+def _same(a, b):
+    for x, y in zip(a, b):
+        if isinstance(x, tuple):
+            assert all(np.array_equal(u, v) for u, v in zip(x, y))
+        else:
+            assert np.array_equal(x, y)
+
+
+def test_checkpoint_restore_continues_bit_identically():
+    a = _make(recompute_every=7)
+    b = _make(recompute_every=7)
+    try:
+        pt.pt_sweep(a, 20, 1)
+        blob = pt.pt_checkpoint(a)
+        pt.pt_sweep(a, 30, 1)
+        pt.pt_restore(b, blob)
+        pt.pt_sweep(b, 30, 1)
+        _same(_state(a), _state(b))
+        assert pt.pt_counters(a) == pt.pt_counters(b)
+    finally:
+        pt.pt_destroy(a)
+        pt.pt_destroy(b)
+
+
+@pytest.mark.parametrize("xe", [1, 2, 0])
+def test_split_calls_equal_one_call(xe):
+    a = _make(seed=4)
+    b = _make(seed=4)
+    try:
+        pt.pt_sweep(a, 70, xe)
+        for n in (1, 32, 5, 32):
+            pt.pt_sweep(b, n, xe)
+        _same(_state(a), _state(b))
+    finally:
+        pt.pt_destroy(a)
+        pt.pt_destroy(b)
+
+
+def test_batch_equals_separate_contexts():
+    specs = [(20, 4, 1, 0), (45, 7, 2, 1), (33, 3, 3, 2)]
+    made = [pt.make_params(N, inputs.temperature_ladder(0.2, 3.0, R), s, ensemble_id=e,
+                           init_positions=inputs.random_coil(N, R, s, e), n_bins=256)
+            for (N, R, s, e) in specs]
+    hb = pt.pt_create_batch([p for p, _ in made])
+    try:
+        pt.pt_sweep(hb, 25, 1)
+        Eb, Pb, Hb = pt.pt_energies(hb), pt.pt_get_positions(hb), pt.pt_histograms(hb)
+    finally:
+        pt.pt_destroy(hb)
+    eo = po = ho = 0
+    for (N, R, s, e), (p, _) in zip(specs, made):
+        h = pt.pt_create_ex(p)
+        try:
+            pt.pt_sweep(h, 25, 1)
+            assert np.array_equal(pt.pt_energies(h), Eb[eo:eo + R])
+            assert np.array_equal(pt.pt_get_positions(h), Pb[po:po + 3 * R * N])
+            assert np.array_equal(pt.pt_histograms(h), Hb[ho:ho + R * 256])
+        finally:
+            pt.pt_destroy(h)
+        eo += R
+        po += 3 * R * N
+        ho += R * 256
+
+
+def test_invalid_arguments_are_rejected():
+    T = np.array([0.5, 1.0])
+    with pytest.raises(pt.PtError):
+        pt.pt_create(1, 2, T, 1)  # N < 2
+    with pytest.raises(pt.PtError):
+        pt.pt_create(10, 2, np.array([0.5, -1.0]), 1)
+    with pytest.raises(pt.PtError):
+        pt.pt_create(10, 2, np.array([0.5, np.nan]), 1)
+    bad = inputs.random_coil(10, 2, 1)
+    bad[1, 5] += 5.0  # stretches two bonds far beyond the FENE window
+    p, keep = pt.make_params(10, T, 1, init_positions=bad)
+    with pytest.raises(pt.PtError):
+        pt.pt_create_ex(p)
+    h = pt.pt_create(10, 2, T, 1)
+    try:
+        with pytest.raises(pt.PtError):
+            pt.pt_sweep(h, -1, 1)
+        assert pt.lib().pt_energies(h, None, 2) == pt.PT_EINVAL
+        out = np.zeros(3)
+        assert pt.lib().pt_energies(h, out.ctypes.data, 3) == pt.PT_EINVAL
+        with pytest.raises(pt.PtError):
+            pt.pt_set_positions(h, bad)
+        pt.pt_sweep(h, 5, 1)  # still usable after rejected calls
+        assert np.all(np.isfinite(pt.pt_energies(h)))
+    finally:
+        pt.pt_destroy(h)
+    pt.pt_destroy(None)
+
+
+def test_library_coil_is_valid():
+    h = pt.pt_create(200, 3, np.array([0.5, 1.0, 2.0]), 99)
+    try:
+        x = pt.pt_get_positions(h).reshape(3, 200, 3).astype(np.float64)
+        b = np.linalg.norm(x[:, 1:] - x[:, :-1], axis=2)
+        assert np.all(np.abs(b - 0.7) < 1e-5)
+        for r in range(3):
+            d = np.linalg.norm(x[r, :, None] - x[r, None, :], axis=2)
+            iu = np.triu_indices(200, 2)
+            assert d[iu].min() >= 0.7 - 1e-5
+        E = pt.pt_energies(h)
+        for r in range(3):
+            assert E[r] == pytest.approx(oracle.full_energy(x[r].astype(np.float32)), rel=1e-12, abs=1e-10)
+    finally:
+        pt.pt_destroy(h)

@@ -1,0 +1,150 @@
+"""CUDA path vs the FP64 oracle, through the C-ABI, on the same seeded inputs.
+
+Per move: same bead (bit-exact), dE within 1e-6 + 1e-5 |dE|, same decision outside the
+tolerance margin; per sweep: tracked energies within the summed per-move tolerances,
+same exchange decisions. Where no decision fell inside the margin, final conformations,
+labels and histograms must be identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1107_3490_gb300 import inputs, pt
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(N, R, S, seed, xe=1, delta=0.3, lj_bonded=1, tmin=0.3, tmax=3.0, recompute_every=0,
+         n_bins=512, e_min=None, e_max=None, ens_id=0):
+    T = inputs.temperature_ladder(tmin, tmax, R)
+    x0 = inputs.random_coil(N, R, seed, ens_id)
+    e_min = -8.0 * N if e_min is None else e_min
+    e_max = 2.0 * N if e_max is None else e_max
+    p, keep = pt.make_params(N, T, seed, ensemble_id=ens_id, init_positions=x0, delta=delta,
+                             lj_bonded=lj_bonded, recompute_every=recompute_every, n_bins=n_bins,
+                             e_min=e_min, e_max=e_max)
+    h = pt.pt_create_ex(p)
+    try:
+        pt.pt_set_debug_log(h, 0, S)
+        pt.pt_sweep(h, S, xe)
+        g = pt.pt_get_debug_log(h, S)
+        out = dict(E=pt.pt_energies(h), pos=pt.pt_get_positions(h).reshape(R, N, 3),
+                   rot=pt.pt_get_permutation(h), hist=pt.pt_histograms(h).reshape(R, n_bins),
+                   mom=pt.pt_moments(h), outl=pt.pt_hist_outliers(h), acc=pt.pt_acceptance(h),
+                   drift=pt.pt_drift(h), counters=pt.pt_counters(h, 0))
+    finally:
+        pt.pt_destroy(h)
+    orc = oracle.OracleEnsemble(x0, T, seed, ensemble_id=ens_id, delta=delta, lj_bonded=lj_bonded,
+                                recompute_every=recompute_every, n_bins=n_bins, e_min=e_min,
+                                e_max=e_max, threads=8)
+    o = parity.oracle_log_with_labels(orc, S, xe)
+    rep = parity.compare(g, o, R, N, T, seed, ens_id)
+    return rep, out, orc
+
+
+def _full_match(rep, out, orc, S):
+    """No divergence: the two chains are the same chain."""
+    assert rep.sweeps_compared == S
+    assert np.array_equal(out["pos"], orc.pos)
+    assert np.array_equal(out["rot"], orc.rep_of_temp)
+    np.testing.assert_allclose(out["E"], orc.energies_by_temperature(), rtol=0,
+                               atol=max(1e-9, 2 * rep.max_e_err + 1e-12))
+    mv_att, mv_acc, ex_att, ex_acc = out["acc"]
+    assert np.array_equal(mv_att, orc.mv_att) and np.array_equal(mv_acc, orc.mv_acc)
+    R = orc.R
+    assert np.array_equal(ex_att[: R - 1], orc.ex_att[: R - 1])
+    assert np.array_equal(ex_acc[: R - 1], orc.ex_acc[: R - 1])
+    # histograms: identical counts except where an energy sat within the tolerance of a bin
+    # edge; totals always identical
+    assert np.array_equal(out["hist"].sum(1) + out["outl"].sum(1), orc.hist.sum(1) + orc.outl.sum(1))
+    assert np.abs(out["hist"] - orc.hist).sum() <= 2
+    np.testing.assert_allclose(out["mom"][:, 0], orc.mom[:, 0], rtol=0, atol=0)
+    np.testing.assert_allclose(out["mom"][:, 1], orc.mom[:, 1], rtol=1e-9, atol=S * rep.max_e_err + 1e-9)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_trajectory_n30_r16_100_sweeps(seed):
+    """The small plain-PT configuration (N = 30, 16 replicas, T 0.3-3.0, delta 0.3,
+    exchange every sweep): first 100 sweeps move for move."""
+    rep, out, orc = _run(30, 16, 100, seed)
+    assert rep.ok, rep.failures
+    print(f"seed {seed}: {rep.sweeps_compared} sweeps, {rep.moves_compared} moves, "
+          f"max dE err/tol {rep.max_ratio:.3f}, divergence {rep.divergence}")
+    assert rep.sweeps_compared >= 20
+    if rep.divergence is None:
+        _full_match(rep, out, orc, 100)
+
+
+@pytest.mark.parametrize("N,R,S", [(2, 1, 60), (2, 3, 60), (3, 2, 60), (31, 3, 20), (33, 5, 20),
+                                   (64, 2, 12), (65, 3, 10), (100, 4, 8)])
+def test_ragged_and_edge_sizes(N, R, S):
+    rep, out, orc = _run(N, R, S, seed=11 + N)
+    assert rep.ok, rep.failures
+    if rep.divergence is None:
+        _full_match(rep, out, orc, S)
+
+
+def test_lj_between_non_bonded_only():
+    rep, out, orc = _run(40, 6, 30, seed=5, lj_bonded=0)
+    assert rep.ok, rep.failures
+    if rep.divergence is None:
+        _full_match(rep, out, orc, 30)
+
+
+def test_paper_displacement_0_01():
+    rep, out, orc = _run(30, 8, 40, seed=9, delta=0.01)
+    assert rep.ok, rep.failures
+    assert rep.max_ratio < 1.0
+
+
+@pytest.mark.parametrize("xe", [0, 3])
+def test_exchange_schedules(xe):
+    rep, out, orc = _run(25, 6, 30, seed=21, xe=xe)
+    assert rep.ok, rep.failures
+    if rep.divergence is None:
+        _full_match(rep, out, orc, 30)
+        assert out["counters"][1] == orc.xround
+
+
+@pytest.mark.parametrize("N,R,S", [(300, 4, 4), (1000, 2, 2)])
+def test_long_chains(N, R, S):
+    rep, out, orc = _run(N, R, S, seed=3, tmin=0.2)
+    assert rep.ok, rep.failures
+    assert rep.moves_compared > 0
+
+
+def test_periodic_fp64_recompute():
+    rep, out, orc = _run(40, 4, 30, seed=8, recompute_every=10)
+    assert rep.ok, rep.failures
+    if rep.divergence is None:
+        _full_match(rep, out, orc, 30)
+        # after a recompute both sides hold Eq. 4 of the same float coordinates
+        np.testing.assert_allclose(out["E"], orc.energies_by_temperature(), rtol=1e-12, atol=1e-10)
+    assert np.all(out["drift"] < 1e-4)
+
+
+def test_initial_energies_and_energy_entry_point():
+    rng_sizes = [2, 3, 33, 100, 1000]
+    T = np.array([1.0])
+    h = pt.pt_create(10, 1, T, 1)
+    try:
+        for N in rng_sizes:
+            x = inputs.random_coil(N, 3, 100 + N)
+            e = pt.pt_energy_fp64(h, x)
+            for c in range(3):
+                ref = oracle.full_energy(x[c])
+                assert e[c] == pytest.approx(ref, rel=1e-11, abs=1e-10)
+            e0 = pt.pt_energy_fp64(h, x, lj_bonded=0)
+            assert e0[0] == pytest.approx(oracle.full_energy(x[0], 0), rel=1e-11, abs=1e-10)
+    finally:
+        pt.pt_destroy(h)
+    x = inputs.random_coil(50, 4, 7)
+    p, keep = pt.make_params(50, inputs.temperature_ladder(0.3, 3, 4), 7, init_positions=x)
+    h = pt.pt_create_ex(p)
+    try:
+        E = pt.pt_energies(h)
+        for r in range(4):
+            assert E[r] == pytest.approx(oracle.full_energy(x[r]), rel=1e-12, abs=1e-10)
+    finally:
+        pt.pt_destroy(h)

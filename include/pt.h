@@ -159,6 +159,26 @@ int pt_get_debug_log(pt_ctx* h, int32_t* bead, float* de, float* theta, uint8_t*
 int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonded,
                    double* out);
 
+/* Allocation-free FP64 total energy (Eq. 4), for callers that must not allocate GPU memory
+ * themselves or through us: a host application whose own pooling allocator has reserved
+ * the device memory, a latency-critical loop that cannot afford an allocation's implicit
+ * synchronisation, or a plug-in environment where only the host application allocates.
+ * The paper has no counterpart; it is the allocation-free twin of pt_energy_fp64.
+ *   conf:  DEVICE (or managed) memory, [n_conf][N][3] float coordinates, caller-owned.
+ *   out:   DEVICE (or managed) memory, [n_conf] doubles, caller-owned.
+ *   stream: cudaStream_t to enqueue on (NULL: the default stream); the call is asynchronous.
+ * The partial sums live in one fixed device array of PT_NOALLOC_SCRATCH_DOUBLES doubles
+ * (1 MiB) compiled into the library: every GPU that loads the library keeps it until the
+ * process exits. A call needs n_conf * c(N) doubles of it, c(N) = min(64, max(1, N / 8));
+ * larger calls are rejected with PT_EINVAL (split them). No cudaMalloc / cudaFree or other
+ * allocating routine is called. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. All calls share the array and every call overwrites the slots it
+ * uses, so calls whose kernels overlap on the GPU race: serialise them. */
+#define PT_NOALLOC_SCRATCH_DOUBLES 131072
+int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, double* out,
+                           void* stream);
+
 /* Kernel timing for profiling: with on = 1 every sweep-kernel launch is bracketed by CUDA
  * events on the context's stream (inside the captured graph too). pt_kernel_timing then
  * reports the mean duration of the sweep launches of the most recent graph replay (or of

@@ -37,6 +37,11 @@ struct EnsHost {
 
 }  // namespace
 
+namespace ptgb {
+// Error reporting for entry points defined in other translation units.
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace ptgb
+
 struct pt_ctx {
     std::vector<EnsHost> ens;
     std::vector<RepDev> reps;

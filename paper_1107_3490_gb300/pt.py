@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libptgb.so")
 
 PT_OK, PT_EINVAL, PT_ENOMEM, PT_ECUDA, PT_ESTATE, PT_ETIMEOUT, PT_EBUSY = 0, -1, -2, -3, -4, -5, -6
 PT_MAX_N = 8192
+PT_NOALLOC_SCRATCH_DOUBLES = 131072
 
 
 class PtError(RuntimeError):
@@ -65,6 +66,7 @@ _SIGS = {
     "pt_set_debug_log": (_I, [_V, _I64, _I64]),
     "pt_get_debug_log": (_I, [_V, _V, _V, _V, _V, _V, _V]),
     "pt_energy_fp64": (_I, [_V, _V, _I, _I, _I, _V]),
+    "pt_energy_fp64_noalloc": (_I, [_V, _I, _I, _I, _V, _V]),
     "pt_set_kernel_timing": (_I, [_V, _I]),
     "pt_kernel_timing": (_I, [_V, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "pt_checkpoint": (_I, [_V, _V, ctypes.POINTER(ctypes.c_size_t)]),
@@ -261,6 +263,13 @@ def pt_energy_fp64(h, conf, lj_bonded: int = 1) -> np.ndarray:
     out = np.zeros(c.shape[0], dtype=np.float64)
     _ck(lib().pt_energy_fp64(h, _p(c), c.shape[1], c.shape[0], int(lj_bonded), _p(out)))
     return out
+
+
+def pt_energy_fp64_noalloc(conf_dev_ptr: int, N: int, n_conf: int, lj_bonded: int, out_dev_ptr: int,
+                           stream: int = 0) -> None:
+    """Allocation-free FP64 energies of conformations already in device memory (pointers)."""
+    _ck(lib().pt_energy_fp64_noalloc(conf_dev_ptr, int(N), int(n_conf), int(lj_bonded), out_dev_ptr,
+                                     stream or None))
 
 
 def pt_set_kernel_timing(h, on: bool) -> None:

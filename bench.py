@@ -204,6 +204,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     made = ensemble_params(rank)
     h = pt.pt_create_batch([p for p, _ in made], stream.cuda_stream)
+    pt.pt_set_sweep_kernel(h, args.kernel)
     pt.pt_set_kernel_timing(h, True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB of L2
 
@@ -268,6 +269,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": f"ensembles per GPU, {ws} GPU(s), no collective",
                        "l2": "256 MB buffer written between timed steps (outside the per-step events)",
+                       "sweep_kernel": "lookahead groups of 8 moves" if args.kernel == 1 else "one move at a time",
                        "pair_evals_per_s": value * 2 * (N_BEADS - 1)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "clocks": clocks}
@@ -288,6 +290,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", type=int, default=0, choices=[0, 1],
+                    help="sweep kernel: 0 one move at a time (default), 1 lookahead groups")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -179,10 +179,15 @@ int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonde
 int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, double* out,
                            void* stream);
 
+/* Choose the sweep kernel: 0 = one move at a time (default), 1 = groups of up to 8
+ * consecutive moves with distinct beads evaluated together. Both run the same chain, move
+ * for move; they differ only in the summation order of dE. */
+int pt_set_sweep_kernel(pt_ctx* h, int variant);
+
 /* Kernel timing for profiling: with on = 1 every sweep-kernel launch is bracketed by CUDA
  * events on the context's stream (inside the captured graph too). pt_kernel_timing then
- * reports the mean duration of the sweep launches of the most recent graph replay (or of
- * the last <= 64 direct launches) and how many launches that mean covers. */
+ * reports the mean duration of the sweep launches that did work in the most recent graph
+ * replay (or of the last <= 64 direct launches) and how many launches that mean covers. */
 int pt_set_kernel_timing(pt_ctx* h, int on);
 int pt_kernel_timing(pt_ctx* h, double* mean_sweep_ms, int* n_launches);
 

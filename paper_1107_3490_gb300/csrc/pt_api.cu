@@ -46,6 +46,7 @@ struct pt_ctx {
     std::vector<EnsHost> ens;
     std::vector<RepDev> reps;
     int G = 0, P = 0, nmax = 0, warps = 1, num_sms = 152;
+    int variant = kSweepSimple;
     int64_t H = 0;
     int64_t done = 0;  // sweeps done by every ensemble (they advance together)
     State S{};
@@ -240,11 +241,11 @@ int upload_positions(pt_ctx* h, const std::vector<float>& xyz) {
 
 // Sweep launch, bracketed by a timing event pair when timing is on.
 cudaError_t timed_sweep(pt_ctx* h, int chunk) {
-    if (h->tev.empty()) return launch_sweep(h->S, chunk, h->warps, h->stream);
+    if (h->tev.empty()) return launch_sweep(h->S, chunk, h->warps, h->variant, h->stream);
     const int i = h->t_next;
     // External records stay visible to the host when captured into a graph.
     cudaError_t e = cudaEventRecordWithFlags(h->tev[2 * i], h->stream, cudaEventRecordExternal);
-    if (e == cudaSuccess) e = launch_sweep(h->S, chunk, h->warps, h->stream);
+    if (e == cudaSuccess) e = launch_sweep(h->S, chunk, h->warps, h->variant, h->stream);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(h->tev[2 * i + 1], h->stream, cudaEventRecordExternal);
     h->t_next = (i + 1) % kTimingSlots;
     h->t_count = std::min(h->t_count + 1, kTimingSlots);
@@ -413,8 +414,8 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
         pt_destroy(h);
         return nullptr;
     }
-    h->warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms);
-    ce = configure_sweep(h->nmax, h->warps);
+    h->warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, h->variant);
+    ce = configure_sweep(h->nmax, h->warps, h->variant);
     if (ce != cudaSuccess) {
         fail(PT_ECUDA, "configure sweep kernel: %s", cudaGetErrorString(ce));
         pt_destroy(h);
@@ -558,7 +559,9 @@ extern "C" int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every) {
         for (int64_t i = 0; i < (n_sweeps + kGraphSweeps - 1) / kGraphSweeps; ++i)
             CK(h, cudaGraphLaunch(h->graph1, h->stream));
         h->t_graph = true;
-        h->t_count = h->tev.empty() ? 0 : kGraphSweeps;
+        // the last replay runs n % kGraphSweeps real sweeps first; the rest return at once
+        const int real = (int)(n_sweeps % kGraphSweeps == 0 ? kGraphSweeps : n_sweeps % kGraphSweeps);
+        h->t_count = h->tev.empty() ? 0 : real;
     } else {
         if (h->t_graph) {
             h->t_graph = false;
@@ -576,6 +579,19 @@ extern "C" int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every) {
         }
     }
     h->done += n_sweeps;
+    return PT_OK;
+}
+
+extern "C" int pt_set_sweep_kernel(pt_ctx* h, int variant) {
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (variant != kSweepSimple && variant != kSweepLookahead) return fail(PT_EINVAL, "unknown sweep kernel %d", variant);
+    if ((rc = sync_and_check(h))) return rc;
+    const int warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, variant);
+    CK(h, configure_sweep(h->nmax, warps, variant));
+    h->variant = variant;
+    h->warps = warps;
+    drop_graph(h);
     return PT_OK;
 }
 

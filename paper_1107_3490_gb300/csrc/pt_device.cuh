@@ -84,15 +84,32 @@ __device__ __forceinline__ df df_mul(df x, df y) {
     e = __fmaf_rn(x.lo, y.hi, e);
     return fast_two_sum(p.hi, e);
 }
+// Quotient and square root start from the hardware approximations (relative error about
+// 2^-22) and take one correction step in double-float arithmetic (Dekker / Karp-Markstein
+// style refinement), which brings the result to about 2^-44 relative.
+__device__ __forceinline__ float rcp_approx_f(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx_f(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ df df_div(df n, df d) {
-    float q1 = __fdiv_rn(n.hi, d.hi);
-    df r = df_sub(n, df_mul(d, df{q1, 0.f}));
-    return fast_two_sum(q1, __fdiv_rn(r.hi, d.hi));
+    const float r = rcp_approx_f(d.hi);
+    const float q1 = __fmul_rn(n.hi, r);
+    // residual n - q1 d, exact in its leading part through the FMA
+    float e = __fmaf_rn(-q1, d.hi, n.hi);
+    e = __fadd_rn(e, __fmaf_rn(-q1, d.lo, n.lo));
+    return fast_two_sum(q1, __fmul_rn(e, r));
 }
 __device__ __forceinline__ df df_sqrt(df a) {
-    float s = __fsqrt_rn(a.hi);
-    float r = __fadd_rn(__fmaf_rn(-s, s, a.hi), a.lo);
-    return fast_two_sum(s, __fdiv_rn(r, __fmul_rn(2.f, s)));
+    const float y = rsqrt_approx_f(a.hi);
+    const float s = __fmul_rn(a.hi, y);
+    const float e = __fadd_rn(__fmaf_rn(-s, s, a.hi), a.lo);
+    return fast_two_sum(s, __fmul_rn(e, __fmul_rn(0.5f, y)));
 }
 __device__ __forceinline__ float df_f(df a) { return __fadd_rn(a.hi, a.lo); }
 

@@ -62,10 +62,13 @@ struct State {
 };
 
 // Launchers (pt_kernels.cu). All are asynchronous on `st`.
-int sweep_warps_per_block(int nmax, int n_reps, int num_sms);
-size_t sweep_smem_bytes(int nmax, int warps);
-cudaError_t configure_sweep(int nmax, int warps);  // once per context, before any capture
-cudaError_t launch_sweep(const State& s, int chunk, int warps, cudaStream_t st);
+// Sweep kernels: kSweepSimple evaluates one move at a time; kSweepLookahead evaluates
+// groups of moves together (same chain, move for move).
+enum : int { kSweepSimple = 0, kSweepLookahead = 1 };
+int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant);
+size_t sweep_smem_bytes(int nmax, int warps, int variant);
+cudaError_t configure_sweep(int nmax, int warps, int variant);  // per context, before any capture
+cudaError_t launch_sweep(const State& s, int chunk, int warps, int variant, cudaStream_t st);
 cudaError_t launch_exchange(const State& s, cudaStream_t st);
 
 // FP64 total energy (Eq. 4) of n_conf conformations. Conformation c has N_c beads at

@@ -49,6 +49,40 @@ __device__ double warp_full_energy(const float4* P, int N, int lj_bonded, int la
     return warp_sum_d(e);
 }
 
+
+// End of one sweep of replica g (all lanes of its warp call it): the periodic FP64
+// recompute of Eq. 4, then the measurement into the replica's temperature slot (the
+// replica owns the slot until the next exchange, so plain read-modify-write is race-free)
+// and the move counters.
+__device__ __forceinline__ void sweep_epilogue(const State& S, const EnsDev& ed, int g, int gs, int slot, int N,
+                                               const float4* P, int lane, int64_t s, int nacc, bool logging,
+                                               double& E) {
+    if (ed.recompute_every > 0 && (s + 1) % ed.recompute_every == 0) {
+        const double full = warp_full_energy(P, N, ed.lj_bonded, lane);
+        if (lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
+        E = full;
+    }
+    if (lane == 0) {
+        if (!isfinite(E)) {
+            atomicOr(S.err, kErrNonFinite);
+        } else if (s >= ed.n_therm) {
+            if (E < ed.e_min) {
+                S.outl[2 * gs] += 1.0;
+            } else {
+                const double b = floor((E - ed.e_min) * ed.inv_w);
+                if (b >= (double)ed.n_bins) S.outl[2 * gs + 1] += 1.0;
+                else S.hist[ed.hist_base + (int64_t)slot * ed.n_bins + (int64_t)b] += 1.0;
+            }
+            S.mom[3 * gs] += 1.0;
+            S.mom[3 * gs + 1] += E;
+            S.mom[3 * gs + 2] += E * E;
+        }
+        S.mv_att[gs] += (unsigned long long)N;
+        S.mv_acc[gs] += (unsigned long long)nacc;
+        if (logging) S.log_e[(size_t)(s - S.log_s0) * S.n_reps + g] = E;
+    }
+}
+
 __global__ void __launch_bounds__(128) k_sweep(State S, int chunk) {
     extern __shared__ float4 smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -158,36 +192,313 @@ __global__ void __launch_bounds__(128) k_sweep(State S, int chunk) {
             }
         }
         E = (E + (double)dsum.hi) + (double)dsum.lo;
-        // ---- periodic FP64 recompute of Eq. 4
-        if (ed.recompute_every > 0 && (s + 1) % ed.recompute_every == 0) {
-            const double full = warp_full_energy(P, N, ed.lj_bonded, lane);
-            if (lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
-            E = full;
-        }
-        if (lane == 0) {
-            if (!isfinite(E)) {
-                atomicOr(S.err, kErrNonFinite);
-            } else if (s >= ed.n_therm) {
-                // ---- measurement in the replica's temperature slot (it owns the slot
-                // until the next exchange, so plain read-modify-write is race-free)
-                if (E < ed.e_min) {
-                    S.outl[2 * gs] += 1.0;
-                } else {
-                    const double b = floor((E - ed.e_min) * ed.inv_w);
-                    if (b >= (double)ed.n_bins) S.outl[2 * gs + 1] += 1.0;
-                    else S.hist[ed.hist_base + (int64_t)slot * ed.n_bins + (int64_t)b] += 1.0;
-                }
-                S.mom[3 * gs] += 1.0;
-                S.mom[3 * gs + 1] += E;
-                S.mom[3 * gs + 2] += E * E;
-            }
-            S.mv_att[gs] += (unsigned long long)N;
-            S.mv_acc[gs] += (unsigned long long)nacc;
-            if (logging) S.log_e[(size_t)(s - S.log_s0) * S.n_reps + g] = E;
-        }
+        sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
     }
     __syncwarp();
     for (int i = lane; i < N; i += 32) S.pos[rd.pos_off + i] = P[i];
+    if (lane == 0) {
+        S.E[g] = E;
+        S.rep_sweep[g] = s_end;
+    }
+}
+
+
+// ---- lookahead sweep --------------------------------------------------------------------
+// The same chain as k_sweep, move for move, with the per-move latency spread over a group
+// of up to W consecutive moves whose beads are distinct. Because the beads are distinct,
+// the old position of each group bead is its position at the start of the group, and only
+// the pair terms between group beads depend on the outcome of earlier moves of the group.
+// So: (1) every move's FP32 row over the non-group partners is evaluated against the start
+// positions, W moves per partner load (instruction-level parallelism); (2) one double-float
+// pass evaluates the steep pairs, the bonds to non-group partners and, for every ordered
+// pair of group moves (i, l), the term of i with l unmoved (variant 0) and, for l < i, with
+// l moved (variant 1); (3) one interleaved butterfly reduces all W rows; (4) the W Metropolis
+// decisions run in order, each adding the variant its earlier moves selected.
+constexpr int kLaW = 8;    // moves per group
+constexpr int kLaQ = 64;   // queued steep pairs per move (further ones are evaluated inline)
+constexpr int kEntBond = 0, kEntSteep = 1, kEntCorr0 = 2, kEntCorr1 = 3;
+
+__host__ __device__ constexpr int la_ent_cap() { return kLaW * (2 + kLaQ) + 2 * kLaW * kLaW; }
+// float4 units per warp: chain, group old/new positions, then the integer / float arrays
+__host__ __device__ inline size_t la_warp_f4(int nmax) {
+    const size_t words = (size_t)kLaW * kLaQ + 2 * (size_t)la_ent_cap() + 2 * kLaW * kLaW + (kLaW + 1);
+    return (size_t)nmax + 2 * kLaW + (words + 3) / 4;
+}
+
+__global__ void __launch_bounds__(128) k_sweep_la(State S, int chunk) {
+    constexpr int W = kLaW;
+    extern __shared__ float4 smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (g >= S.n_reps) return;
+    const RepDev rd = S.reps[g];
+    const EnsDev ed = S.ens[rd.ens];
+    const int N = rd.N;
+    float4* P = smem + (size_t)warp * la_warp_f4(S.nmax);
+    float4* GP = P + S.nmax;   // [W] start position of group bead i, .w = bead index bits
+    float4* GPN = GP + W;      // [W] proposed position of group bead i
+    int* Q = reinterpret_cast<int*>(GPN + W);  // [W][kLaQ] queued steep partners
+    int* ENT = Q + W * kLaQ;                   // [cap] double-float entries
+    float* RES = reinterpret_cast<float*>(ENT + la_ent_cap());  // [cap] entry values
+    float* CORR = RES + la_ent_cap();          // [2][W][W] group-pair terms
+    int* SEG = reinterpret_cast<int*>(CORR + 2 * W * W);  // [W + 1] entry segments
+
+    int64_t s = S.rep_sweep[g];
+    const int64_t s_end = min(ed.target, s + (int64_t)chunk);
+    if (s >= s_end) return;
+
+    for (int i = lane; i < N; i += 32) {
+        float4 q = S.pos[rd.pos_off + i];
+        q.w = 0.f;  // .w marks group beads inside this kernel
+        P[i] = q;
+    }
+    __syncwarp();
+
+    double E = S.E[g];
+    const int slot = S.temp_of_rep[g];
+    const int gs = rd.slot_base + slot;
+    const float Tf = S.Tf[gs];
+    const uint32_t k0 = (uint32_t)ed.seed, k1 = (uint32_t)(ed.seed >> 32);
+    const uint32_t c3 = ed.ens_id | (kTagMove << 24);
+    const bool ljb = ed.lj_bonded != 0;
+    const float delta = ed.delta;
+    const float kInf = __int_as_float(0x7f800000);
+
+    for (; s < s_end; ++s) {
+        const bool logging = S.log_bead && s >= S.log_s0 && s < S.log_s0 + S.log_ns;
+        const size_t lrow = logging ? (size_t)(s - S.log_s0) * S.log_pstride + rd.pos_off : 0;
+        df dsum = {0.f, 0.f};
+        int nacc = 0;
+        for (int m0 = 0; m0 < N; m0 += 32) {
+            int km = 0;
+            float sx = 0.f, sy = 0.f, sz = 0.f, th = 0.f;
+            if (m0 + lane < N) {
+                const uint32_t m = (uint32_t)(m0 + lane);
+                u4 w4 = philox(u4{2u * m, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                u4 v4 = philox(u4{2u * m + 1u, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                km = (int)__umulhi(w4.x, (uint32_t)N);
+                sx = __fsub_rn(__fmul_rn(2.f, unif24(w4.y)), 1.f);
+                sy = __fsub_rn(__fmul_rn(2.f, unif24(w4.z)), 1.f);
+                sz = __fsub_rn(__fmul_rn(2.f, unif24(w4.w)), 1.f);
+                th = __fmul_rn(-logf(unif24(v4.x)), Tf);
+            }
+            const int mc = min(32, N - m0);
+            for (int i0 = 0; i0 < mc;) {
+                // ---- group: consecutive moves from i0 until a bead repeats (at most W)
+                bool conflict = false;
+#pragma unroll
+                for (int d = 1; d < W; ++d) {
+                    const int kp = __shfl_up_sync(kFull, km, d);
+                    if (lane - d >= i0 && kp == km) conflict = true;
+                }
+                const unsigned cm = __ballot_sync(kFull, conflict && lane > i0 && lane < i0 + W && lane < mc);
+                int w = min(W, mc - i0);
+                if (cm) w = min(w, __ffs(cm) - 1 - i0);
+
+                const int src = min(i0 + lane, 31);
+                const int kl = __shfl_sync(kFull, km, src);
+                const float ulx = __shfl_sync(kFull, sx, src), uly = __shfl_sync(kFull, sy, src),
+                            ulz = __shfl_sync(kFull, sz, src);
+                if (lane < w) {
+                    const float4 q = P[kl];
+                    GP[lane] = make_float4(q.x, q.y, q.z, __int_as_float(kl));
+                    GPN[lane] = make_float4(__fadd_rn(q.x, __fmul_rn(delta, ulx)), __fadd_rn(q.y, __fmul_rn(delta, uly)),
+                                            __fadd_rn(q.z, __fmul_rn(delta, ulz)), 0.f);
+                }
+                for (int t = lane; t < 2 * W * W; t += 32) CORR[t] = 0.f;
+                __syncwarp();
+                if (lane < w) P[kl].w = 1.f;  // group flag (beads are distinct)
+                float3 p[W], pn[W];
+                int kg[W];
+                float thg[W];
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    const float4 a = GP[i], b = GPN[i];
+                    p[i] = make_float3(a.x, a.y, a.z);
+                    pn[i] = make_float3(b.x, b.y, b.z);
+                    kg[i] = i < w ? __float_as_int(a.w) : -8;
+                    thg[i] = __shfl_sync(kFull, th, min(i0 + i, 31));
+                }
+                __syncwarp();
+
+                // ---- (1) FP32 rows of all group moves over the non-group partners
+                float acc[W];
+                int qn[W];
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    acc[i] = 0.f;
+                    qn[i] = 0;
+                }
+                for (int j0 = 0; j0 < N; j0 += 32) {
+                    const int j = j0 + lane;
+                    const float4 q = P[min(j, N - 1)];
+                    const bool live = j < N && q.w == 0.f;
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        if (i < w) {
+                            const float dxo = __fsub_rn(q.x, p[i].x), dyo = __fsub_rn(q.y, p[i].y),
+                                        dzo = __fsub_rn(q.z, p[i].z);
+                            const float dxn = __fsub_rn(q.x, pn[i].x), dyn = __fsub_rn(q.y, pn[i].y),
+                                        dzn = __fsub_rn(q.z, pn[i].z);
+                            const float r2o = __fmaf_rn(dzo, dzo, __fmaf_rn(dyo, dyo, __fmul_rn(dxo, dxo)));
+                            const float r2n = __fmaf_rn(dzn, dzn, __fmaf_rn(dyn, dyn, __fmul_rn(dxn, dxn)));
+                            const bool ord = live && (unsigned)(j - kg[i] + 1) > 2u;
+                            const bool steep = ord && fminf(r2o, r2n) < kSteep2f;
+                            const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
+                            const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
+                            if (ord && !steep)
+                                acc[i] = __fmaf_rn(__fsub_rn(xn, xo), __fmaf_rn(kAf, __fadd_rn(xn, xo), -kBf), acc[i]);
+                            const unsigned bm = __ballot_sync(kFull, steep);
+                            if (bm) {
+                                if (steep) {
+                                    const int at = qn[i] + __popc(bm & lanemask_lt());
+                                    if (at < kLaQ) {
+                                        Q[i * kLaQ + at] = j;
+                                    } else {
+                                        bool brk = false;
+                                        acc[i] = __fadd_rn(acc[i], pair_term_accurate(q, p[i], pn[i], true, false, &brk));
+                                    }
+                                }
+                                qn[i] += __popc(bm);
+                            }
+                        }
+                    }
+                }
+                // ---- (3) reduce all rows at once (every lane ends with every sum)
+#pragma unroll
+                for (int m = 16; m; m >>= 1)
+#pragma unroll
+                    for (int i = 0; i < W; ++i) acc[i] = __fadd_rn(acc[i], __shfl_xor_sync(kFull, acc[i], m));
+
+                // ---- (2) double-float entries, in a fixed order
+                int ne = 0;
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    if (lane == 0) SEG[i] = ne;
+                    if (i < w) {
+                        const int kb = lane == 0 ? kg[i] - 1 : kg[i] + 1;
+                        const bool want = lane < 2 && kb >= 0 && kb < N && P[kb].w == 0.f;
+                        const unsigned bm = __ballot_sync(kFull, want);
+                        if (want) ENT[ne + __popc(bm & lanemask_lt())] = kb | (i << 16) | (kEntBond << 24);
+                        ne += __popc(bm);
+                        const int nq = min(qn[i], kLaQ);
+                        for (int t = lane; t < nq; t += 32) ENT[ne + t] = Q[i * kLaQ + t] | (i << 16) | (kEntSteep << 24);
+                        ne += nq;
+                    }
+                }
+                if (lane == 0) SEG[W] = ne;
+                // group pairs: FP32 term written straight away unless steep or bonded
+                for (int e0 = 0; e0 < 2 * W * W; e0 += 32) {
+                    const int e = e0 + lane;
+                    const int v = e / (W * W), i = (e / W) % W, l = e % W;
+                    bool want = false;
+                    if (i < w && l < w && i != l && (v == 0 || l < i)) {
+                        const float4 a = GP[i], b = GPN[i], c = v ? GPN[l] : GP[l];
+                        const int ki = __float_as_int(a.w), kk = __float_as_int(GP[l].w);
+                        const bool bonded = ki - kk == 1 || kk - ki == 1;
+                        const float ex = __fsub_rn(c.x, a.x), ey = __fsub_rn(c.y, a.y), ez = __fsub_rn(c.z, a.z);
+                        const float fx = __fsub_rn(c.x, b.x), fy = __fsub_rn(c.y, b.y), fz = __fsub_rn(c.z, b.z);
+                        const float r2o = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
+                        const float r2n = __fmaf_rn(fz, fz, __fmaf_rn(fy, fy, __fmul_rn(fx, fx)));
+                        want = bonded || fminf(r2o, r2n) < kSteep2f;
+                        if (!want) {
+                            const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
+                            const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
+                            CORR[v * W * W + i * W + l] =
+                                __fmul_rn(__fsub_rn(xn, xo), __fmaf_rn(kAf, __fadd_rn(xn, xo), -kBf));
+                        }
+                    }
+                    const unsigned bm = __ballot_sync(kFull, want);
+                    if (want) ENT[ne + __popc(bm & lanemask_lt())] = l | (i << 16) | ((v ? kEntCorr1 : kEntCorr0) << 24);
+                    ne += __popc(bm);
+                }
+                __syncwarp();
+                for (int t = lane; t < ne; t += 32) {
+                    const int code = ENT[t];
+                    const int kind = code >> 24, i = (code >> 16) & 0xff, x = code & 0xffff;
+                    const float4 a = GP[i], b = GPN[i];
+                    const int ki = __float_as_int(a.w);
+                    float4 q;
+                    bool bonded;
+                    if (kind <= kEntSteep) {
+                        q = P[x];
+                        bonded = kind == kEntBond;
+                    } else {
+                        q = kind == kEntCorr1 ? GPN[x] : GP[x];
+                        const int kx = __float_as_int(GP[x].w);
+                        bonded = ki - kx == 1 || kx - ki == 1;
+                    }
+                    bool brk = false;
+                    float v = pair_term_accurate(q, make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                                 bonded ? ljb : true, bonded, &brk);
+                    if (brk) v = kInf;
+                    if (kind <= kEntSteep) RES[t] = v;
+                    else CORR[(kind - kEntCorr0) * W * W + i * W + x] = v;
+                }
+                __syncwarp();
+                float mine = 0.f;  // lane i: sum of its move's bond and steep entries
+                if (lane < w)
+                    for (int t = SEG[lane]; t < SEG[lane + 1]; ++t) mine = __fadd_rn(mine, RES[t]);
+
+                // ---- (4) decisions in move order (every lane computes the same)
+                float dEg[W];
+                unsigned amask = 0;
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    dEg[i] = 0.f;
+                    const float ent = __shfl_sync(kFull, mine, i);
+                    if (i < w) {
+                        float d = __fadd_rn(acc[i], ent);
+#pragma unroll
+                        for (int l = i + 1; l < W; ++l)
+                            if (l < w) d = __fadd_rn(d, CORR[i * W + l]);
+#pragma unroll
+                        for (int l = 0; l < i; ++l)
+                            d = __fadd_rn(d, ((amask >> l) & 1u) ? CORR[W * W + i * W + l] : CORR[i * W + l]);
+                        dEg[i] = d;
+                        if (d < thg[i]) amask |= 1u << i;
+                    }
+                }
+                // ---- commit
+                float my_dE = 0.f, my_th = 0.f;
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    if (lane == i) {
+                        my_dE = dEg[i];
+                        my_th = thg[i];
+                    }
+                    if (i < w && ((amask >> i) & 1u)) dsum = df_add(dsum, df{dEg[i], 0.f});
+                }
+                nacc += __popc(amask);
+                if (lane < w) {
+                    const int k = __float_as_int(GP[lane].w);
+                    if ((amask >> lane) & 1u) {
+                        const float4 b = GPN[lane];
+                        P[k] = make_float4(b.x, b.y, b.z, 0.f);
+                    } else {
+                        P[k].w = 0.f;
+                    }
+                    if (logging) {
+                        const size_t li = lrow + m0 + i0 + lane;
+                        S.log_bead[li] = k;
+                        S.log_de[li] = my_dE;
+                        S.log_theta[li] = my_th;
+                        S.log_acc[li] = (amask >> lane) & 1u;
+                    }
+                }
+                __syncwarp();
+                i0 += w;
+            }
+        }
+        E = (E + (double)dsum.hi) + (double)dsum.lo;
+        sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
+    }
+    __syncwarp();
+    for (int i = lane; i < N; i += 32) {
+        float4 q = P[i];
+        q.w = 0.f;
+        S.pos[rd.pos_off + i] = q;
+    }
     if (lane == 0) {
         S.E[g] = E;
         S.rep_sweep[g] = s_end;
@@ -293,28 +604,34 @@ __global__ void k_energy_final(const double* __restrict__ scratch, int n_conf, i
 }
 
 // ---- launchers ----------------------------------------------------------------------------
-size_t sweep_smem_bytes(int nmax, int warps) {
-    return (size_t)warps * ((size_t)nmax + (size_t)(nmax + 3) / 4) * sizeof(float4);
+size_t sweep_smem_bytes(int nmax, int warps, int variant) {
+    const size_t per_warp = variant == kSweepLookahead ? la_warp_f4(nmax) : (size_t)nmax + (size_t)(nmax + 3) / 4;
+    return (size_t)warps * per_warp * sizeof(float4);
 }
 
-int sweep_warps_per_block(int nmax, int n_reps, int num_sms) {
+int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant) {
     int w = 4;
-    while (w > 1 && sweep_smem_bytes(nmax, w) > 200 * 1024) w >>= 1;
+    while (w > 1 && sweep_smem_bytes(nmax, w, variant) > 200 * 1024) w >>= 1;
     // few replicas: spread them over the SMs instead of packing them
     while (w > 1 && (n_reps + w - 1) / w < 2 * num_sms) w >>= 1;
     return w;
 }
 
-cudaError_t configure_sweep(int nmax, int warps) {
-    const size_t smem = sweep_smem_bytes(nmax, warps);
+cudaError_t configure_sweep(int nmax, int warps, int variant) {
+    const size_t smem = sweep_smem_bytes(nmax, warps, variant);
     if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return variant == kSweepLookahead
+               ? cudaFuncSetAttribute(k_sweep_la, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+               : cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-cudaError_t launch_sweep(const State& s, int chunk, int warps, cudaStream_t st) {
-    const size_t smem = sweep_smem_bytes(s.nmax, warps);
+cudaError_t launch_sweep(const State& s, int chunk, int warps, int variant, cudaStream_t st) {
+    const size_t smem = sweep_smem_bytes(s.nmax, warps, variant);
     const int blocks = (s.n_reps + warps - 1) / warps;
-    k_sweep<<<blocks, 32 * warps, smem, st>>>(s, chunk);
+    if (variant == kSweepLookahead)
+        k_sweep_la<<<blocks, 32 * warps, smem, st>>>(s, chunk);
+    else
+        k_sweep<<<blocks, 32 * warps, smem, st>>>(s, chunk);
     return cudaGetLastError();
 }
 

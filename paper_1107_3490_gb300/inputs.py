@@ -45,8 +45,9 @@ def random_coil(n_beads: int, n_replicas: int, seed: int, ensemble_id: int = 0,
     rng = _rng(seed, 0xC011, int(ensemble_id))
     R, N = n_replicas, n_beads
     pos = np.zeros((R, N, 3), dtype=np.float64)
+    alive = np.ones(R, dtype=bool)  # chains still growing (not trapped)
     for i in range(1, N):
-        todo = np.arange(R)
+        todo = np.nonzero(alive)[0]
         for _ in range(max_tries):
             v = rng.standard_normal((todo.size, 3))
             v /= np.linalg.norm(v, axis=1, keepdims=True)
@@ -60,11 +61,12 @@ def random_coil(n_beads: int, n_replicas: int, seed: int, ensemble_id: int = 0,
             todo = todo[~ok]
             if todo.size == 0:
                 break
-        if todo.size:
-            # trapped walks: restart those chains from scratch with a fresh stream
-            sub = random_coil(N, todo.size, seed, (int(ensemble_id) + 1) * 7919 + i, max_tries)
-            pos[todo] = sub.astype(np.float64)
-            return _finish(pos)
+        alive[todo] = False  # trapped walks stop here and are regrown below
+    dead = np.nonzero(~alive)[0]
+    if dead.size:
+        # regrow trapped chains from scratch with their own stream
+        sub = random_coil(N, dead.size, seed, (int(ensemble_id) + 1) * 7919 + int(dead[0]), max_tries)
+        pos[dead] = sub.astype(np.float64)
     return _finish(pos)
 
 

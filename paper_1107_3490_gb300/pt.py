@@ -67,6 +67,7 @@ _SIGS = {
     "pt_get_debug_log": (_I, [_V, _V, _V, _V, _V, _V, _V]),
     "pt_energy_fp64": (_I, [_V, _V, _I, _I, _I, _V]),
     "pt_energy_fp64_noalloc": (_I, [_V, _I, _I, _I, _V, _V]),
+    "pt_set_sweep_kernel": (_I, [_V, _I]),
     "pt_set_kernel_timing": (_I, [_V, _I]),
     "pt_kernel_timing": (_I, [_V, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "pt_checkpoint": (_I, [_V, _V, ctypes.POINTER(ctypes.c_size_t)]),
@@ -270,6 +271,11 @@ def pt_energy_fp64_noalloc(conf_dev_ptr: int, N: int, n_conf: int, lj_bonded: in
     """Allocation-free FP64 energies of conformations already in device memory (pointers)."""
     _ck(lib().pt_energy_fp64_noalloc(conf_dev_ptr, int(N), int(n_conf), int(lj_bonded), out_dev_ptr,
                                      stream or None))
+
+
+def pt_set_sweep_kernel(h, variant: int) -> None:
+    """0: one move at a time (default); 1: lookahead groups of moves."""
+    _ck(lib().pt_set_sweep_kernel(h, int(variant)))
 
 
 def pt_set_kernel_timing(h, on: bool) -> None:

@@ -14,9 +14,16 @@ from tests import parity
 
 pytestmark = pytest.mark.gpu
 
+KERNELS = {0: "one move at a time", 1: "lookahead groups"}
+
+
+@pytest.fixture(params=sorted(KERNELS), ids=lambda v: f"kernel{v}")
+def variant(request):
+    return request.param
+
 
 def _run(N, R, S, seed, xe=1, delta=0.3, lj_bonded=1, tmin=0.3, tmax=3.0, recompute_every=0,
-         n_bins=512, e_min=None, e_max=None, ens_id=0):
+         n_bins=512, e_min=None, e_max=None, ens_id=0, variant=1):
     T = inputs.temperature_ladder(tmin, tmax, R)
     x0 = inputs.random_coil(N, R, seed, ens_id)
     e_min = -8.0 * N if e_min is None else e_min
@@ -26,6 +33,7 @@ def _run(N, R, S, seed, xe=1, delta=0.3, lj_bonded=1, tmin=0.3, tmax=3.0, recomp
                              e_min=e_min, e_max=e_max)
     h = pt.pt_create_ex(p)
     try:
+        pt.pt_set_sweep_kernel(h, variant)
         pt.pt_set_debug_log(h, 0, S)
         pt.pt_sweep(h, S, xe)
         g = pt.pt_get_debug_log(h, S)
@@ -64,10 +72,10 @@ def _full_match(rep, out, orc, S):
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])
-def test_trajectory_n30_r16_100_sweeps(seed):
+def test_trajectory_n30_r16_100_sweeps(seed, variant):
     """The small plain-PT configuration (N = 30, 16 replicas, T 0.3-3.0, delta 0.3,
     exchange every sweep): first 100 sweeps move for move."""
-    rep, out, orc = _run(30, 16, 100, seed)
+    rep, out, orc = _run(30, 16, 100, seed, variant=variant)
     assert rep.ok, rep.failures
     print(f"seed {seed}: {rep.sweeps_compared} sweeps, {rep.moves_compared} moves, "
           f"max dE err/tol {rep.max_ratio:.3f}, divergence {rep.divergence}")
@@ -78,29 +86,29 @@ def test_trajectory_n30_r16_100_sweeps(seed):
 
 @pytest.mark.parametrize("N,R,S", [(2, 1, 60), (2, 3, 60), (3, 2, 60), (31, 3, 20), (33, 5, 20),
                                    (64, 2, 12), (65, 3, 10), (100, 4, 8)])
-def test_ragged_and_edge_sizes(N, R, S):
-    rep, out, orc = _run(N, R, S, seed=11 + N)
+def test_ragged_and_edge_sizes(N, R, S, variant):
+    rep, out, orc = _run(N, R, S, seed=11 + N, variant=variant)
     assert rep.ok, rep.failures
     if rep.divergence is None:
         _full_match(rep, out, orc, S)
 
 
-def test_lj_between_non_bonded_only():
-    rep, out, orc = _run(40, 6, 30, seed=5, lj_bonded=0)
+def test_lj_between_non_bonded_only(variant):
+    rep, out, orc = _run(40, 6, 30, seed=5, lj_bonded=0, variant=variant)
     assert rep.ok, rep.failures
     if rep.divergence is None:
         _full_match(rep, out, orc, 30)
 
 
-def test_paper_displacement_0_01():
-    rep, out, orc = _run(30, 8, 40, seed=9, delta=0.01)
+def test_paper_displacement_0_01(variant):
+    rep, out, orc = _run(30, 8, 40, seed=9, delta=0.01, variant=variant)
     assert rep.ok, rep.failures
     assert rep.max_ratio < 1.0
 
 
 @pytest.mark.parametrize("xe", [0, 3])
-def test_exchange_schedules(xe):
-    rep, out, orc = _run(25, 6, 30, seed=21, xe=xe)
+def test_exchange_schedules(xe, variant):
+    rep, out, orc = _run(25, 6, 30, seed=21, xe=xe, variant=variant)
     assert rep.ok, rep.failures
     if rep.divergence is None:
         _full_match(rep, out, orc, 30)
@@ -108,14 +116,14 @@ def test_exchange_schedules(xe):
 
 
 @pytest.mark.parametrize("N,R,S", [(300, 4, 4), (1000, 2, 2)])
-def test_long_chains(N, R, S):
-    rep, out, orc = _run(N, R, S, seed=3, tmin=0.2)
+def test_long_chains(N, R, S, variant):
+    rep, out, orc = _run(N, R, S, seed=3, tmin=0.2, variant=variant)
     assert rep.ok, rep.failures
     assert rep.moves_compared > 0
 
 
-def test_periodic_fp64_recompute():
-    rep, out, orc = _run(40, 4, 30, seed=8, recompute_every=10)
+def test_periodic_fp64_recompute(variant):
+    rep, out, orc = _run(40, 4, 30, seed=8, recompute_every=10, variant=variant)
     assert rep.ok, rep.failures
     if rep.divergence is None:
         _full_match(rep, out, orc, 30)
@@ -148,3 +156,29 @@ def test_initial_energies_and_energy_entry_point():
             assert E[r] == pytest.approx(oracle.full_energy(x[r]), rel=1e-12, abs=1e-10)
     finally:
         pt.pt_destroy(h)
+
+
+def test_kernels_agree_on_a_hot_dense_case():
+    """Both kernels on a case with many steep pairs and group collisions (N = 12, delta 0.3,
+    T up to 5): same beads and decisions; dE equal within the tolerance of each other."""
+    logs = []
+    for v in (0, 1):
+        T = inputs.temperature_ladder(0.3, 5.0, 8)
+        x0 = inputs.random_coil(12, 8, 77)
+        p, keep = pt.make_params(12, T, 77, init_positions=x0, recompute_every=0)
+        h = pt.pt_create_ex(p)
+        try:
+            pt.pt_set_sweep_kernel(h, v)
+            pt.pt_set_debug_log(h, 0, 50)
+            pt.pt_sweep(h, 50, 1)
+            logs.append(pt.pt_get_debug_log(h, 50))
+        finally:
+            pt.pt_destroy(h)
+    a, b = logs
+    assert np.array_equal(a["bead"], b["bead"])
+    same = np.array_equal(a["acc"], b["acc"])
+    if same:
+        fin = np.isfinite(a["de"])
+        assert np.array_equal(fin, np.isfinite(b["de"]))
+        d = np.abs(a["de"][fin].astype(np.float64) - b["de"][fin])
+        assert np.all(d <= 2e-6 + 2e-5 * np.abs(a["de"][fin]))

@@ -209,3 +209,18 @@ def test_metropolis_threshold_acceptance_rate():
             rate = np.mean(de < th)
             expect = min(1.0, math.exp(-de / T))
             assert rate == pytest.approx(expect, abs=4 * math.sqrt(expect * (1 - expect) / len(th)) + 1e-4)
+
+
+def test_random_coil_inputs_are_valid_even_when_walks_trap():
+    """Every chain of the input generator has all bonds at r0 and non-bonded distances >= r0,
+    also for long chains where some random walks get trapped and are regrown."""
+    from paper_1107_3490_gb300 import inputs
+    for N, R, seed in ((1000, 128, 1), (300, 16, 3), (2, 4, 1)):
+        x = inputs.random_coil(N, R, seed).astype(np.float64)
+        b = np.linalg.norm(x[:, 1:] - x[:, :-1], axis=2)
+        assert np.all(np.abs(b - 0.7) < 1e-5), (N, R, seed)
+        if 3 <= N <= 300:
+            for r in range(R):
+                d = np.linalg.norm(x[r, :, None] - x[r, None, :], axis=2)
+                iu = np.triu_indices(N, 2)
+                assert d[iu].min() >= 0.7 - 1e-5

@@ -269,7 +269,8 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": f"ensembles per GPU, {ws} GPU(s), no collective",
                        "l2": "256 MB buffer written between timed steps (outside the per-step events)",
-                       "sweep_kernel": "lookahead groups of 8 moves" if args.kernel == 1 else "one move at a time",
+                       "sweep_kernel": {0: "warp per replica", 1: "lookahead groups of 8 moves",
+                                        2: "team of warps per replica", 3: "warp per move of a group"}[args.kernel],
                        "pair_evals_per_s": value * 2 * (N_BEADS - 1)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "clocks": clocks}
@@ -290,8 +291,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", type=int, default=0, choices=[0, 1],
-                    help="sweep kernel: 0 one move at a time (default), 1 lookahead groups")
+    ap.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="sweep kernel: 0 warp per replica (default), 1 lookahead groups, 2 team of warps, "
+                         "3 warp per move of a group")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -179,9 +179,12 @@ int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonde
 int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, double* out,
                            void* stream);
 
-/* Choose the sweep kernel: 0 = one move at a time (default), 1 = groups of up to 8
- * consecutive moves with distinct beads evaluated together. Both run the same chain, move
- * for move; they differ only in the summation order of dE. */
+/* Choose the sweep kernel: 0 = one warp per replica, one move at a time (default);
+ * 1 = one warp per replica, groups of up to 8 consecutive moves with distinct beads
+ * evaluated together; 2 = a CTA of 1-8 warps per replica (by N), one move at a time;
+ * 3 = a CTA of 2-8 warps per replica, each warp evaluating one move of a group of moves with
+ * distinct beads. All run the same chain, move for move; they differ only in the summation
+ * order of dE. */
 int pt_set_sweep_kernel(pt_ctx* h, int variant);
 
 /* Kernel timing for profiling: with on = 1 every sweep-kernel launch is bracketed by CUDA

@@ -585,7 +585,8 @@ extern "C" int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every) {
 extern "C" int pt_set_sweep_kernel(pt_ctx* h, int variant) {
     int rc = check_usable(h);
     if (rc) return rc;
-    if (variant != kSweepSimple && variant != kSweepLookahead) return fail(PT_EINVAL, "unknown sweep kernel %d", variant);
+    if (variant < kSweepSimple || variant > kSweepWpm)
+        return fail(PT_EINVAL, "unknown sweep kernel %d", variant);
     if ((rc = sync_and_check(h))) return rc;
     const int warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, variant);
     CK(h, configure_sweep(h->nmax, warps, variant));

@@ -162,10 +162,32 @@ __device__ __forceinline__ float pair_term_accurate(float4 q, float3 p, float3 p
 }
 
 // ---- FP32 fast path -------------------------------------------------------------------
-__device__ __forceinline__ float rcp_approx(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
+__device__ __forceinline__ float rcp_approx(float x) { return rcp_approx_f(x); }
+
+// Threshold of the team kernel's LJ fast path (0.68^2) and of its FP32 FENE path
+// (|r - r0| < 0.2 before and after the move). A float32 emulation of the row against the
+// FP64 oracle on thermalised chains (N = 30 and 100, delta = 0.3) kept every move within
+// 1e-6 + 1e-5 |dE| (worst 0.77 of it) with these limits.
+constexpr double kSteepTeam2 = 0.4624;
+constexpr float kSteepTeam2f = (float)kSteepTeam2;
+constexpr float kFeneUmaxF = 0.2f;
+
+// FENE difference in FP32 without cancellation: r_o - r_n = (r_o^2 - r_n^2) / (r_o + r_n)
+// with r_o^2 - r_n^2 = d . (2 (q - p) - d), d = pn - p, so that
+// w_n / w_o - 1 = (u_o^2 - u_n^2) / w_o = (r_o - r_n)(u_o + u_n) / ((R - u_o)(R + u_o)).
+// Valid when |u| < kFeneUmaxF on both sides (then no bond can break).
+__device__ __forceinline__ float fene_diff_f32(float4 q, float3 p, float3 pn, float r2o, float r2n) {
+    const float dx = __fsub_rn(pn.x, p.x), dy = __fsub_rn(pn.y, p.y), dz = __fsub_rn(pn.z, p.z);
+    const float sx = __fsub_rn(__fmul_rn(2.f, __fsub_rn(q.x, p.x)), dx);
+    const float sy = __fsub_rn(__fmul_rn(2.f, __fsub_rn(q.y, p.y)), dy);
+    const float sz = __fsub_rn(__fmul_rn(2.f, __fsub_rn(q.z, p.z)), dz);
+    const float dr2 = __fmaf_rn(dz, sz, __fmaf_rn(dy, sy, __fmul_rn(dx, sx)));
+    const float ro = __fsqrt_rn(r2o), rn = __fsqrt_rn(r2n);
+    const float uo = __fsub_rn(ro, (float)kR0), un = __fsub_rn(rn, (float)kR0);
+    const float drr = __fdividef(dr2, __fadd_rn(ro, rn));
+    const float wo = __fmul_rn(__fsub_rn((float)kRF, uo), __fadd_rn((float)kRF, uo));
+    const float z = __fdividef(__fmul_rn(drr, __fadd_rn(uo, un)), wo);
+    return __fmul_rn(-(float)kFeneC, log1pf(z));
 }
 
 // ---- FP64 pair energy for the full recompute (Eq. 4) --------------------------------------

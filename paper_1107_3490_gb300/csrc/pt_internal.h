@@ -64,7 +64,9 @@ struct State {
 // Launchers (pt_kernels.cu). All are asynchronous on `st`.
 // Sweep kernels: kSweepSimple evaluates one move at a time; kSweepLookahead evaluates
 // groups of moves together (same chain, move for move).
-enum : int { kSweepSimple = 0, kSweepLookahead = 1 };
+// kSweepTeam gives each replica a CTA of several warps (one move at a time).
+// kSweepWpm gives each replica a CTA whose warps each evaluate one move of a group.
+enum : int { kSweepSimple = 0, kSweepLookahead = 1, kSweepTeam = 2, kSweepWpm = 3 };
 int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant);
 size_t sweep_smem_bytes(int nmax, int warps, int variant);
 cudaError_t configure_sweep(int nmax, int warps, int variant);  // per context, before any capture

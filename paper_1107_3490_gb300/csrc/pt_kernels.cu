@@ -505,6 +505,474 @@ __global__ void __launch_bounds__(128) k_sweep_la(State S, int chunk) {
     }
 }
 
+
+// ---- team sweep ---------------------------------------------------------------------------
+// One CTA of NW warps owns one replica, one move at a time. The draws of the next 32 NW
+// moves are made in parallel (one per thread) into shared memory. Per move: every thread
+// takes partners tid, tid + 2 T, ... two at a time (independent chains for ILP), steep
+// pairs go to a per-warp queue evaluated in double-float by the same warp, and warp 0 adds
+// the two bonds (FP32 FENE without cancellation when both bond lengths stay within 0.2 of
+// r0, double-float otherwise). Each warp's butterfly sum goes to shared memory; after the one
+// barrier of the move every thread adds the NW partials in the same order and takes the same
+// decision. Thread 0 stores an accepted position; until the next barrier makes that store
+// visible, every thread substitutes the accepted position for that bead itself (forwarding).
+__device__ __forceinline__ float lj_term_f32(float r2o, float r2n) {
+    const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
+    const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
+    return __fmul_rn(__fsub_rn(xn, xo), __fmaf_rn(kAf, __fadd_rn(xn, xo), -kBf));
+}
+__device__ __forceinline__ float r2_f32(float4 q, float3 p) {
+    const float dx = __fsub_rn(q.x, p.x), dy = __fsub_rn(q.y, p.y), dz = __fsub_rn(q.z, p.z);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+// Double-float paths are rare; keeping them out of line keeps the hot loops small.
+__device__ __noinline__ float lj_diff_df(float4 q, float3 p, float3 pn) {
+    return df_f(df_sub(lj_df(r2_df(q, pn)), lj_df(r2_df(q, p))));
+}
+__device__ __noinline__ float bond_term_df(float4 q, float3 p, float3 pn, bool lj, bool lj_fast, float r2o, float r2n,
+                                          bool* broken) {
+    const df a = r2_df(q, p), b = r2_df(q, pn);
+    const float f = fene_diff_df(a, b);
+    if (isinf(f)) {
+        *broken = true;
+        return 0.f;
+    }
+    return lj ? __fadd_rn(f, lj_fast ? lj_term_f32(r2o, r2n) : df_f(df_sub(lj_df(b), lj_df(a)))) : f;
+}
+// Bonded partner q of the moved bead: FENE (Eq. 3) plus, if lj, the LJ term.
+__device__ __forceinline__ float bond_term_team(float4 q, float3 p, float3 pn, bool lj, bool* broken) {
+    const float r2o = r2_f32(q, p), r2n = r2_f32(q, pn);
+    const float uo = __fsub_rn(__fsqrt_rn(r2o), (float)kR0), un = __fsub_rn(__fsqrt_rn(r2n), (float)kR0);
+    const bool fene_fast = fmaxf(fabsf(uo), fabsf(un)) < kFeneUmaxF;
+    const bool lj_fast = fminf(r2o, r2n) >= kSteepTeam2f;
+    if (!fene_fast) return bond_term_df(q, p, pn, lj, lj_fast, r2o, r2n, broken);
+    float t = fene_diff_f32(q, p, pn, r2o, r2n);
+    if (lj) t = __fadd_rn(t, lj_fast ? lj_term_f32(r2o, r2n) : lj_diff_df(q, p, pn));
+    return t;
+}
+
+// Queued steep pairs of one warp, two lanes per pair (old and new side in parallel);
+// returns this lane's share (the even lane of each pair holds the difference).
+__device__ __noinline__ df lj_side_df(float4 q, float3 x) { return lj_df(r2_df(q, x)); }
+__device__ __forceinline__ float steep_pairs(const int* Q, int qn, const float4* P, float3 p, float3 pn, int kf,
+                                             float4 pf, int lane) {
+    float acc = 0.f;
+    const int side = lane & 1;
+    for (int e0 = 0; e0 < qn; e0 += 16) {
+        const int e = e0 + (lane >> 1);
+        df v = {0.f, 0.f};
+        if (e < qn) {
+            const int j = Q[e];
+            const float4 q = j == kf ? pf : P[j];
+            v = lj_side_df(q, side ? pn : p);
+        }
+        const float nh = __shfl_sync(kFull, v.hi, lane | 1), nl = __shfl_sync(kFull, v.lo, lane | 1);
+        if (e < qn && side == 0) acc = __fadd_rn(acc, df_f(df_sub(df{nh, nl}, v)));
+    }
+    return acc;
+}
+
+// Row of the moved bead over four partners per thread (independent chains). A partner
+// counts if it is in range, not flagged (live) and not bonded to k. A pair beyond the
+// cutoff before and after the move contributes exactly 0, so a chunk in which no lane
+// has a partner within the cutoff skips the LJ arithmetic; steep pairs are queued.
+struct RowAcc {
+    float a[4];
+    int qn;
+};
+// kf / pf: a bead whose latest position is in registers, not yet in shared memory (-1: none).
+__device__ __forceinline__ void row4(const float4* P, int N, int k, float3 p, float3 pn, const int (&j)[4],
+                                     bool check_flag, int kf, float4 pf, int* Q, RowAcc& r) {
+    float4 q[4];
+    float r2o[4], r2n[4];
+    bool near[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        q[u] = j[u] == kf ? pf : P[min(j[u], N - 1)];
+        r2o[u] = r2_f32(q[u], p);
+        r2n[u] = r2_f32(q[u], pn);
+        const bool ord = j[u] < N && (!check_flag || q[u].w == 0.f) && (unsigned)(j[u] - k + 1) > 2u;
+        near[u] = ord && fminf(r2o[u], r2n[u]) < kRc2f;
+    }
+    if (__any_sync(kFull, near[0] || near[1] || near[2] || near[3])) {
+        float t[4];
+        bool st[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            st[u] = near[u] && fminf(r2o[u], r2n[u]) < kSteepTeam2f;
+            t[u] = lj_term_f32(r2o[u], r2n[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (near[u] && !st[u]) r.a[u] = __fadd_rn(r.a[u], t[u]);
+            const unsigned bm = __ballot_sync(kFull, st[u]);
+            if (st[u]) Q[r.qn + __popc(bm & lanemask_lt())] = j[u];
+            r.qn += __popc(bm);
+        }
+    }
+}
+
+__host__ __device__ inline int team_qstride(int nmax, int T) { return 32 * ((nmax + T - 1) / T); }
+__host__ __device__ inline size_t team_smem_bytes(int nmax, int nw) {
+    const int T = 32 * nw;
+    return (size_t)nmax * sizeof(float4) + (size_t)T * 6 * 4 + (size_t)2 * nw * 4 +
+           (size_t)nw * team_qstride(nmax, T) * 4 + (size_t)((nmax + 15) / 16) * 16;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_sweep_team(State S, int chunk) {
+    constexpr int T = NW * 32;
+    extern __shared__ float4 smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = blockIdx.x;
+    if (g >= S.n_reps) return;  // whole CTA
+    const RepDev rd = S.reps[g];
+    const EnsDev ed = S.ens[rd.ens];
+    const int N = rd.N;
+    float4* P = smem;
+    int* DK = reinterpret_cast<int*>(P + S.nmax);  // draws of the current batch of T moves
+    float* DX = reinterpret_cast<float*>(DK + T);
+    float* DY = DX + T;
+    float* DZ = DY + T;
+    float* DT = DZ + T;
+    float* BT = DT + T;    // bond terms of the batch's moves, from the positions at batch start
+    float* PART = BT + T;  // [2][NW] warp partial sums, double-buffered by move parity
+    int* Q0 = reinterpret_cast<int*>(PART + 2 * NW);
+    int* Q = Q0 + warp * team_qstride(S.nmax, T);
+    unsigned char* MOV = reinterpret_cast<unsigned char*>(Q0 + NW * team_qstride(S.nmax, T));  // moved in batch
+
+    int64_t s = S.rep_sweep[g];
+    const int64_t s_end = min(ed.target, s + (int64_t)chunk);
+    if (s >= s_end) return;  // uniform over the CTA
+
+    for (int i = tid; i < N; i += T) P[i] = S.pos[rd.pos_off + i];
+
+    double E = S.E[g];
+    const int slot = S.temp_of_rep[g];
+    const int gs = rd.slot_base + slot;
+    const float Tf = S.Tf[gs];
+    const uint32_t k0 = (uint32_t)ed.seed, k1 = (uint32_t)(ed.seed >> 32);
+    const uint32_t c3 = ed.ens_id | (kTagMove << 24);
+    const bool ljb = ed.lj_bonded != 0;
+    const float delta = ed.delta;
+    const float kInf = __int_as_float(0x7f800000);
+    int kprev = -4;  // last move: bead, outcome, new position (forwarded until stored)
+    bool aprev = false;
+    float4 pnprev = make_float4(0.f, 0.f, 0.f, 0.f);
+    int par = 0;
+
+    for (; s < s_end; ++s) {
+        const bool logging = S.log_bead && s >= S.log_s0 && s < S.log_s0 + S.log_ns;
+        const size_t lrow = logging ? (size_t)(s - S.log_s0) * S.log_pstride + rd.pos_off : 0;
+        df dsum = {0.f, 0.f};
+        int nacc = 0;
+        for (int m0 = 0; m0 < N; m0 += T) {
+            __syncthreads();  // the last store of the previous batch is visible
+            for (int i = tid; i < N; i += T) MOV[i] = 0;
+            if (m0 + tid < N) {
+                const uint32_t m = (uint32_t)(m0 + tid);
+                const u4 w4 = philox(u4{2u * m, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                const u4 v4 = philox(u4{2u * m + 1u, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                const int kk = (int)__umulhi(w4.x, (uint32_t)N);
+                const float ux = __fsub_rn(__fmul_rn(2.f, unif24(w4.y)), 1.f);
+                const float uy = __fsub_rn(__fmul_rn(2.f, unif24(w4.z)), 1.f);
+                const float uz = __fsub_rn(__fmul_rn(2.f, unif24(w4.w)), 1.f);
+                DK[tid] = kk;
+                DX[tid] = ux;
+                DY[tid] = uy;
+                DZ[tid] = uz;
+                DT[tid] = __fmul_rn(-logf(unif24(v4.x)), Tf);
+                // bond terms of this move against the positions at batch start; used unless
+                // the bead or a bonded neighbour moves earlier in the batch
+                const float4 q = P[kk];
+                const float3 pk = make_float3(q.x, q.y, q.z);
+                const float3 pnk = make_float3(__fadd_rn(q.x, __fmul_rn(delta, ux)), __fadd_rn(q.y, __fmul_rn(delta, uy)),
+                                               __fadd_rn(q.z, __fmul_rn(delta, uz)));
+                bool brk = false;
+                float bt = 0.f;
+                if (kk > 0) bt = bond_term_team(P[kk - 1], pk, pnk, ljb, &brk);
+                if (kk + 1 < N) bt = __fadd_rn(bt, bond_term_team(P[kk + 1], pk, pnk, ljb, &brk));
+                BT[tid] = brk ? kInf : bt;
+            }
+            __syncthreads();
+            const int mc = min(T, N - m0);
+            for (int b = 0; b < mc; ++b) {
+                const int k = DK[b];
+                const float theta = DT[b];
+                float4 p4 = P[k];
+                if (aprev && k == kprev) p4 = pnprev;
+                const float3 p = make_float3(p4.x, p4.y, p4.z);
+                const float3 pn = make_float3(__fadd_rn(p.x, __fmul_rn(delta, DX[b])), __fadd_rn(p.y, __fmul_rn(delta, DY[b])),
+                                              __fadd_rn(p.z, __fmul_rn(delta, DZ[b])));
+                RowAcc ra = {{0.f, 0.f, 0.f, 0.f}, 0};
+                const int kf = aprev ? kprev : -1;
+                for (int j0 = 0; j0 < N; j0 += 4 * T) {
+                    const int jj[4] = {j0 + tid, j0 + T + tid, j0 + 2 * T + tid, j0 + 3 * T + tid};
+                    row4(P, N, k, p, pn, jj, false, kf, pnprev, Q, ra);
+                }
+                int qn = ra.qn;
+                float acc = __fadd_rn(__fadd_rn(ra.a[0], ra.a[1]), __fadd_rn(ra.a[2], ra.a[3]));
+                __syncwarp();
+                // bonds: the batch value unless the bead or a neighbour moved in this batch (the
+                // previous move's flag may not be visible yet, so it is checked from registers)
+                const bool stale = MOV[k] || (k > 0 && MOV[k - 1]) || (k + 1 < N && MOV[k + 1]) ||
+                                   (aprev && (unsigned)(kprev - k + 1) <= 2u);
+                bool broken = false;
+                if (warp == 0) {
+                    if (!stale) {
+                        if (lane == 0) {
+                            const float bt = BT[b];
+                            if (isinf(bt)) broken = true;
+                            else acc = __fadd_rn(acc, bt);
+                        }
+                    } else if (lane < 2) {
+                        const int j = lane == 0 ? k - 1 : k + 1;
+                        if (j >= 0 && j < N) {
+                            float4 q = P[j];
+                            if (aprev && j == kprev) q = pnprev;
+                            acc = __fadd_rn(acc, bond_term_team(q, p, pn, ljb, &broken));
+                        }
+                    }
+                }
+                acc = __fadd_rn(acc, steep_pairs(Q, qn, P, p, pn, kf, pnprev, lane));
+                acc = warp_sum(acc);
+                broken = __any_sync(kFull, broken);
+                if (lane == 0) PART[par * NW + warp] = broken ? kInf : acc;
+                __syncthreads();
+                float dE = PART[par * NW];
+#pragma unroll
+                for (int w = 1; w < NW; ++w) dE = __fadd_rn(dE, PART[par * NW + w]);
+                const bool accept = dE < theta;  // NaN and +inf reject
+                if (accept) {
+                    dsum = df_add(dsum, df{dE, 0.f});
+                    ++nacc;
+                }
+                if (tid == 0) {
+                    if (accept) {
+                        P[k] = make_float4(pn.x, pn.y, pn.z, 0.f);
+                        MOV[k] = 1;
+                    }
+                    if (logging) {
+                        const size_t li = lrow + m0 + b;
+                        S.log_bead[li] = k;
+                        S.log_de[li] = dE;
+                        S.log_theta[li] = theta;
+                        S.log_acc[li] = accept ? 1 : 0;
+                    }
+                }
+                kprev = k;
+                aprev = accept;
+                pnprev = make_float4(pn.x, pn.y, pn.z, 0.f);
+                par ^= 1;
+            }
+        }
+        E = (E + (double)dsum.hi) + (double)dsum.lo;
+        __syncthreads();  // thread 0's last store is visible to warp 0's recompute
+        if (warp == 0) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
+        __syncthreads();
+    }
+    for (int i = tid; i < N; i += T) S.pos[rd.pos_off + i] = P[i];
+    if (tid == 0) {
+        S.E[g] = E;
+        S.rep_sweep[g] = s_end;
+    }
+}
+
+
+// ---- warp-per-move lookahead sweep --------------------------------------------------------
+// One CTA of NW warps owns one replica and keeps up to NW moves in flight: the next moves
+// whose beads are all distinct form a group, and warp i evaluates the whole row of the i-th
+// move of the group against the positions at the start of the group (exact, because no
+// other move of the group touches its bead). The only terms that depend on earlier
+// decisions of the group are the pairs between group beads; warp i evaluates them for move
+// l unmoved (variant 0) and, for l < i, moved (variant 1). After one barrier every thread
+// takes the decisions in move order, adding for each earlier move the variant its outcome
+// selects; then the accepted positions are stored. Same chain as k_sweep, move for move.
+__host__ __device__ inline size_t wpm_smem_bytes(int nmax, int nw) {
+    const int T = 32 * nw;
+    const size_t qcap = 32 * (size_t)((nmax + 31) / 32);
+    return (size_t)nmax * sizeof(float4) + (size_t)T * 5 * 4 + (size_t)2 * nw * sizeof(float4) +
+           (size_t)nw * 4 + (size_t)2 * nw * nw * 4 + (size_t)nw * qcap * 4;
+}
+
+__device__ __forceinline__ float pair_term_team(float4 q, float3 p, float3 pn, bool bonded, bool ljb, bool* broken) {
+    if (bonded) return bond_term_team(q, p, pn, ljb, broken);
+    const float r2o = r2_f32(q, p), r2n = r2_f32(q, pn);
+    return fminf(r2o, r2n) < kSteepTeam2f ? lj_diff_df(q, p, pn) : lj_term_f32(r2o, r2n);
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_sweep_wpm(State S, int chunk) {
+    constexpr int T = NW * 32;
+    extern __shared__ float4 smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = blockIdx.x;
+    if (g >= S.n_reps) return;
+    const RepDev rd = S.reps[g];
+    const EnsDev ed = S.ens[rd.ens];
+    const int N = rd.N;
+    float4* P = smem;
+    float4* GP = P + S.nmax;   // [NW] start position of group bead i, .w = bead index bits
+    float4* GPN = GP + NW;     // [NW] proposed position
+    int* DK = reinterpret_cast<int*>(GPN + NW);
+    float* DX = reinterpret_cast<float*>(DK + T);
+    float* DY = DX + T;
+    float* DZ = DY + T;
+    float* DT = DZ + T;
+    float* SUM = DT + T;        // [NW] row + bond + steep sum of move i
+    float* CORR = SUM + NW;     // [2][NW][NW] group-pair terms
+    const int qcap = 32 * ((S.nmax + 31) / 32);
+    int* Q = reinterpret_cast<int*>(CORR + 2 * NW * NW) + warp * qcap;
+
+    int64_t s = S.rep_sweep[g];
+    const int64_t s_end = min(ed.target, s + (int64_t)chunk);
+    if (s >= s_end) return;
+
+    for (int i = tid; i < N; i += T) {
+        float4 q = S.pos[rd.pos_off + i];
+        q.w = 0.f;  // .w marks group beads inside this kernel
+        P[i] = q;
+    }
+
+    double E = S.E[g];
+    const int slot = S.temp_of_rep[g];
+    const int gs = rd.slot_base + slot;
+    const float Tf = S.Tf[gs];
+    const uint32_t k0 = (uint32_t)ed.seed, k1 = (uint32_t)(ed.seed >> 32);
+    const uint32_t c3 = ed.ens_id | (kTagMove << 24);
+    const bool ljb = ed.lj_bonded != 0;
+    const float delta = ed.delta;
+    const float kInf = __int_as_float(0x7f800000);
+
+    for (; s < s_end; ++s) {
+        const bool logging = S.log_bead && s >= S.log_s0 && s < S.log_s0 + S.log_ns;
+        const size_t lrow = logging ? (size_t)(s - S.log_s0) * S.log_pstride + rd.pos_off : 0;
+        df dsum = {0.f, 0.f};
+        int nacc = 0;
+        for (int m0 = 0; m0 < N; m0 += T) {
+            __syncthreads();  // the previous batch's draws are no longer read
+            if (m0 + tid < N) {
+                const uint32_t m = (uint32_t)(m0 + tid);
+                const u4 w4 = philox(u4{2u * m, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                const u4 v4 = philox(u4{2u * m + 1u, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                DK[tid] = (int)__umulhi(w4.x, (uint32_t)N);
+                DX[tid] = __fsub_rn(__fmul_rn(2.f, unif24(w4.y)), 1.f);
+                DY[tid] = __fsub_rn(__fmul_rn(2.f, unif24(w4.z)), 1.f);
+                DZ[tid] = __fsub_rn(__fmul_rn(2.f, unif24(w4.w)), 1.f);
+                DT[tid] = __fmul_rn(-logf(unif24(v4.x)), Tf);
+            }
+            __syncthreads();
+            const int mc = min(T, N - m0);
+            for (int b = 0; b < mc;) {
+                // ---- group: moves b, b+1, ... while the beads stay distinct (at most NW)
+                int w = 1;
+                for (; w < NW && b + w < mc; ++w) {
+                    const int kw = DK[b + w];
+                    bool rep = false;
+                    for (int l = 0; l < w; ++l) rep |= DK[b + l] == kw;
+                    if (rep) break;
+                }
+                if (tid < w) {
+                    const int k = DK[b + tid];
+                    const float4 q = P[k];
+                    GP[tid] = make_float4(q.x, q.y, q.z, __int_as_float(k));
+                    GPN[tid] = make_float4(__fadd_rn(q.x, __fmul_rn(delta, DX[b + tid])),
+                                           __fadd_rn(q.y, __fmul_rn(delta, DY[b + tid])),
+                                           __fadd_rn(q.z, __fmul_rn(delta, DZ[b + tid])), 0.f);
+                    P[k].w = 1.f;  // own bead only: no conflict between threads
+                }
+                __syncthreads();
+                if (warp < w) {
+                    // ---- the row of move i = warp
+                    const int i = warp;
+                    const float4 gp = GP[i], gpn = GPN[i];
+                    const float3 p = make_float3(gp.x, gp.y, gp.z), pn = make_float3(gpn.x, gpn.y, gpn.z);
+                    const int k = __float_as_int(gp.w);
+                    RowAcc ra = {{0.f, 0.f, 0.f, 0.f}, 0};
+                    for (int j0 = 0; j0 < N; j0 += 128) {
+                        const int jj[4] = {j0 + lane, j0 + 32 + lane, j0 + 64 + lane, j0 + 96 + lane};
+                        row4(P, N, k, p, pn, jj, true, -1, gp, Q, ra);
+                    }
+                    int qn = ra.qn;
+                    float acc = __fadd_rn(__fadd_rn(ra.a[0], ra.a[1]), __fadd_rn(ra.a[2], ra.a[3]));
+                    __syncwarp();
+                    // bonds to non-group partners, then the queued steep pairs
+                    const int kb0 = k - 1, kb1 = k + 1;
+                    const bool b0 = kb0 >= 0 && P[kb0].w == 0.f;
+                    const bool b1 = kb1 < N && P[kb1].w == 0.f;
+                    const int nb = (b0 ? 1 : 0) + (b1 ? 1 : 0);
+                    bool broken = false;
+                    if (lane < nb) {
+                        const int j = (lane == 0 && b0) ? kb0 : kb1;
+                        acc = __fadd_rn(acc, bond_term_team(P[j], p, pn, ljb, &broken));
+                    }
+                    acc = __fadd_rn(acc, steep_pairs(Q, qn, P, p, pn, -1, gp, lane));
+                    acc = warp_sum(acc);
+                    broken = __any_sync(kFull, broken);
+                    if (lane == 0) SUM[i] = broken ? kInf : acc;
+                    // group pairs (i, l): lane 2 l + v; variant 1 only for l < i
+                    const int l = lane >> 1, v = lane & 1;
+                    if (l < w && l != i && (v == 0 || l < i)) {
+                        const float4 q = v ? GPN[l] : GP[l];
+                        const int kl = __float_as_int(GP[l].w);
+                        const bool bonded = kl - k == 1 || k - kl == 1;
+                        bool brk = false;
+                        const float t = pair_term_team(q, p, pn, bonded, ljb, &brk);
+                        CORR[v * NW * NW + i * NW + l] = brk ? kInf : t;
+                    }
+                }
+                __syncthreads();
+                // ---- decisions in move order (every thread computes the same)
+                unsigned amask = 0;
+                float my_dE = 0.f;
+                for (int i = 0; i < w; ++i) {
+                    float d = SUM[i];
+                    for (int l = i + 1; l < w; ++l) d = __fadd_rn(d, CORR[i * NW + l]);
+                    for (int l = 0; l < i; ++l)
+                        d = __fadd_rn(d, ((amask >> l) & 1u) ? CORR[NW * NW + i * NW + l] : CORR[i * NW + l]);
+                    if (d < DT[b + i]) {
+                        amask |= 1u << i;
+                        dsum = df_add(dsum, df{d, 0.f});
+                    }
+                    if (tid == i) my_dE = d;
+                }
+                nacc += __popc(amask);
+                if (tid < w) {
+                    const float4 gp = GP[tid];
+                    const int k = __float_as_int(gp.w);
+                    if ((amask >> tid) & 1u) {
+                        const float4 gpn = GPN[tid];
+                        P[k] = make_float4(gpn.x, gpn.y, gpn.z, 0.f);
+                    } else {
+                        P[k] = make_float4(gp.x, gp.y, gp.z, 0.f);
+                    }
+                    if (logging) {
+                        const size_t li = lrow + m0 + b + tid;
+                        S.log_bead[li] = k;
+                        S.log_de[li] = my_dE;
+                        S.log_theta[li] = DT[b + tid];
+                        S.log_acc[li] = (amask >> tid) & 1u;
+                    }
+                }
+                __syncthreads();
+                b += w;
+            }
+        }
+        E = (E + (double)dsum.hi) + (double)dsum.lo;
+        if (warp == 0) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += T) {
+        float4 q = P[i];
+        q.w = 0.f;
+        S.pos[rd.pos_off + i] = q;
+    }
+    if (tid == 0) {
+        S.E[g] = E;
+        S.rep_sweep[g] = s_end;
+    }
+}
+
 // One exchange round per ensemble that is due (Sec. 3.3, Eq. 6). One warp per ensemble;
 // the pairs of a round are disjoint, so lanes swap labels without conflicts.
 __global__ void k_exchange(State S) {
@@ -605,11 +1073,20 @@ __global__ void k_energy_final(const double* __restrict__ scratch, int n_conf, i
 
 // ---- launchers ----------------------------------------------------------------------------
 size_t sweep_smem_bytes(int nmax, int warps, int variant) {
+    if (variant == kSweepTeam) return team_smem_bytes(nmax, warps);
+    if (variant == kSweepWpm) return wpm_smem_bytes(nmax, warps);
     const size_t per_warp = variant == kSweepLookahead ? la_warp_f4(nmax) : (size_t)nmax + (size_t)(nmax + 3) / 4;
     return (size_t)warps * per_warp * sizeof(float4);
 }
 
+// Team width (warps per replica) for chains of up to nmax beads.
+int team_warps(int nmax) { return nmax <= 48 ? 1 : nmax <= 160 ? 2 : nmax <= 480 ? 4 : 8; }
+// Moves in flight (= warps per replica) of the warp-per-move kernel.
+int wpm_warps(int nmax) { return nmax <= 24 ? 2 : nmax <= 400 ? 4 : 8; }
+
 int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant) {
+    if (variant == kSweepTeam) return team_warps(nmax);
+    if (variant == kSweepWpm) return wpm_warps(nmax);
     int w = 4;
     while (w > 1 && sweep_smem_bytes(nmax, w, variant) > 200 * 1024) w >>= 1;
     // few replicas: spread them over the SMs instead of packing them
@@ -620,6 +1097,23 @@ int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant) {
 cudaError_t configure_sweep(int nmax, int warps, int variant) {
     const size_t smem = sweep_smem_bytes(nmax, warps, variant);
     if (smem <= 48 * 1024) return cudaSuccess;
+    if (variant == kSweepWpm) {
+        const int a = (int)smem;
+        switch (warps) {
+            case 2: return cudaFuncSetAttribute(k_sweep_wpm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+            case 4: return cudaFuncSetAttribute(k_sweep_wpm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+            default: return cudaFuncSetAttribute(k_sweep_wpm<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+        }
+    }
+    if (variant == kSweepTeam) {
+        const int a = (int)smem;
+        switch (warps) {
+            case 1: return cudaFuncSetAttribute(k_sweep_team<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+            case 2: return cudaFuncSetAttribute(k_sweep_team<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+            case 4: return cudaFuncSetAttribute(k_sweep_team<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+            default: return cudaFuncSetAttribute(k_sweep_team<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+        }
+    }
     return variant == kSweepLookahead
                ? cudaFuncSetAttribute(k_sweep_la, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                : cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -627,6 +1121,23 @@ cudaError_t configure_sweep(int nmax, int warps, int variant) {
 
 cudaError_t launch_sweep(const State& s, int chunk, int warps, int variant, cudaStream_t st) {
     const size_t smem = sweep_smem_bytes(s.nmax, warps, variant);
+    if (variant == kSweepWpm) {
+        switch (warps) {
+            case 2: k_sweep_wpm<2><<<s.n_reps, 64, smem, st>>>(s, chunk); break;
+            case 4: k_sweep_wpm<4><<<s.n_reps, 128, smem, st>>>(s, chunk); break;
+            default: k_sweep_wpm<8><<<s.n_reps, 256, smem, st>>>(s, chunk); break;
+        }
+        return cudaGetLastError();
+    }
+    if (variant == kSweepTeam) {
+        switch (warps) {
+            case 1: k_sweep_team<1><<<s.n_reps, 32, smem, st>>>(s, chunk); break;
+            case 2: k_sweep_team<2><<<s.n_reps, 64, smem, st>>>(s, chunk); break;
+            case 4: k_sweep_team<4><<<s.n_reps, 128, smem, st>>>(s, chunk); break;
+            default: k_sweep_team<8><<<s.n_reps, 256, smem, st>>>(s, chunk); break;
+        }
+        return cudaGetLastError();
+    }
     const int blocks = (s.n_reps + warps - 1) / warps;
     if (variant == kSweepLookahead)
         k_sweep_la<<<blocks, 32 * warps, smem, st>>>(s, chunk);

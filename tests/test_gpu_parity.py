@@ -14,7 +14,8 @@ from tests import parity
 
 pytestmark = pytest.mark.gpu
 
-KERNELS = {0: "one move at a time", 1: "lookahead groups"}
+KERNELS = {0: "one move at a time", 1: "lookahead groups", 2: "team of warps per replica",
+           3: "warp per move of a group"}
 
 
 @pytest.fixture(params=sorted(KERNELS), ids=lambda v: f"kernel{v}")
@@ -162,7 +163,7 @@ def test_kernels_agree_on_a_hot_dense_case():
     """Both kernels on a case with many steep pairs and group collisions (N = 12, delta 0.3,
     T up to 5): same beads and decisions; dE equal within the tolerance of each other."""
     logs = []
-    for v in (0, 1):
+    for v in (0, 3):
         T = inputs.temperature_ladder(0.3, 5.0, 8)
         x0 = inputs.random_coil(12, 8, 77)
         p, keep = pt.make_params(12, T, 77, init_positions=x0, recompute_every=0)

@@ -30,6 +30,7 @@ N_BEADS, N_REP, N_ENS, T_MIN, T_MAX = 100, 64, 4, 0.2, 3.0
 SWEEPS_PER_STEP = 1000
 FLOPS_PER_PAIR = 15  # FP32 flops per pair evaluation (FMA = 2), see the design notes
 METRIC = "single-bead Metropolis updates/sec (all replicas)"
+KERNEL_NAMES = {0: "k_sweep", 1: "k_sweep_la", 2: "k_sweep_team", 3: "k_sweep_wpm"}
 UNIT = "updates/s"
 WORKLOAD = (f"PT polymer N={N_BEADS} beads, {N_REP} replicas at T geometric {T_MIN}-{T_MAX}, "
             f"{N_ENS} ensembles (seeds 1-{N_ENS}) per GPU, delta 0.3, exchange every sweep, "
@@ -204,7 +205,11 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     made = ensemble_params(rank)
     h = pt.pt_create_batch([p for p, _ in made], stream.cuda_stream)
-    pt.pt_set_sweep_kernel(h, args.kernel)
+    if args.kernel < 0:
+        kernel = pt.pt_autotune(h, 16)  # untimed; the chain state is restored afterwards
+    else:
+        kernel = args.kernel
+        pt.pt_set_sweep_kernel(h, kernel)
     pt.pt_set_kernel_timing(h, True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB of L2
 
@@ -257,7 +262,7 @@ def run_gpu(args):
     achieved = pairs_per_launch * FLOPS_PER_PAIR / (kernel_ms / 1e3) / 1e12
     peak = fp32_peak_tflops(num_sms, 2070.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_sweep", "launch_ms": kernel_ms, "launches_sampled": kernel_n,
+                "traffic": None, "kernel": KERNEL_NAMES[kernel], "launch_ms": kernel_ms, "launches_sampled": kernel_n,
                 "peak_basis": f"{num_sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)"}
     if clocks and clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / fp32_peak_tflops(num_sms, clocks["sm_mhz"])
@@ -270,7 +275,7 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "parallelism": f"ensembles per GPU, {ws} GPU(s), no collective",
                        "l2": "256 MB buffer written between timed steps (outside the per-step events)",
                        "sweep_kernel": {0: "warp per replica", 1: "lookahead groups of 8 moves",
-                                        2: "team of warps per replica", 3: "warp per move of a group"}[args.kernel],
+                                        2: "team of warps per replica", 3: "warp per move of a group"}[kernel],
                        "pair_evals_per_s": value * 2 * (N_BEADS - 1)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "clocks": clocks}
@@ -291,9 +296,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="sweep kernel: 0 warp per replica (default), 1 lookahead groups, 2 team of warps, "
-                         "3 warp per move of a group")
+    ap.add_argument("--kernel", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help="sweep kernel: -1 autotune (default), 0 warp per replica, 1 lookahead groups, "
+                         "2 team of warps, 3 warp per move of a group")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -187,6 +187,16 @@ int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, 
  * order of dE. */
 int pt_set_sweep_kernel(pt_ctx* h, int variant);
 
+/* The kernel in use (creation picks one from the chain length; see pt_autotune). */
+int pt_get_sweep_kernel(const pt_ctx* h);
+
+/* Autotuner: time every sweep kernel on this context for trial_sweeps sweeps (exchange
+ * every sweep) and keep the fastest. The state is checkpointed before and restored after,
+ * so the chain does not advance. The choice is cached per (GPU name, largest N, replica
+ * count) in the process and, when the environment variable PTGB_AUTOTUNE_CACHE names a
+ * file, in that file; force = 1 measures again. *chosen (may be NULL) gets the kernel. */
+int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen);
+
 /* Kernel timing for profiling: with on = 1 every sweep-kernel launch is bracketed by CUDA
  * events on the context's stream (inside the captured graph too). pt_kernel_timing then
  * reports the mean duration of the sweep launches that did work in the most recent graph

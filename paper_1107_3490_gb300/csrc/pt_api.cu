@@ -5,8 +5,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/pt.h"
@@ -47,6 +51,7 @@ struct pt_ctx {
     std::vector<RepDev> reps;
     int G = 0, P = 0, nmax = 0, warps = 1, num_sms = 152;
     int variant = kSweepSimple;
+    std::string gpu_name;
     int64_t H = 0;
     int64_t done = 0;  // sweeps done by every ensemble (they advance together)
     State S{};
@@ -257,6 +262,11 @@ void drop_graph(pt_ctx* h) {
     h->graph1 = nullptr;
 }
 
+// Kernel choice before any tuning, from timings on GB300 (4 x 64 replicas up to N = 300,
+// 128 replicas above): one warp per replica wins for short chains, the warp-per-move
+// lookahead from about 50 beads on.
+int default_variant(int nmax) { return nmax < 50 ? kSweepSimple : kSweepWpm; }
+
 pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     g_err.clear();
     if (n_ens < 1 || !params) {
@@ -414,6 +424,11 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
         pt_destroy(h);
         return nullptr;
     }
+    {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) h->gpu_name = prop.name;
+    }
+    h->variant = default_variant(h->nmax);
     h->warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, h->variant);
     ce = configure_sweep(h->nmax, h->warps, h->variant);
     if (ce != cudaSuccess) {
@@ -595,6 +610,92 @@ extern "C" int pt_set_sweep_kernel(pt_ctx* h, int variant) {
     drop_graph(h);
     return PT_OK;
 }
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<std::string, int, int>, int> g_tune;  // (GPU, nmax, replicas) -> variant
+
+const char* tune_file() { return std::getenv("PTGB_AUTOTUNE_CACHE"); }
+
+void tune_load() {
+    static bool loaded = false;
+    if (loaded) return;
+    loaded = true;
+    const char* f = tune_file();
+    if (!f) return;
+    FILE* fp = std::fopen(f, "r");
+    if (!fp) return;
+    char name[256];
+    int n, g, v;
+    while (std::fscanf(fp, " %255[^|]|%d|%d|%d", name, &n, &g, &v) == 4) g_tune[{name, n, g}] = v;
+    std::fclose(fp);
+}
+
+void tune_store(const std::string& name, int n, int g, int v) {
+    const char* f = tune_file();
+    if (!f) return;
+    FILE* fp = std::fopen(f, "a");
+    if (!fp) return;
+    std::fprintf(fp, "%s|%d|%d|%d\n", name.c_str(), n, g, v);
+    std::fclose(fp);
+}
+}  // namespace
+
+extern "C" int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen) {
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (trial_sweeps < 1) return fail(PT_EINVAL, "pt_autotune: trial_sweeps must be >= 1");
+    const auto key = std::make_tuple(h->gpu_name, h->nmax, h->G);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load();
+        auto it = g_tune.find(key);
+        if (!force && it != g_tune.end()) {
+            if ((rc = pt_set_sweep_kernel(h, it->second))) return rc;
+            if (chosen) *chosen = it->second;
+            return PT_OK;
+        }
+    }
+    size_t n = 0;
+    if ((rc = pt_checkpoint(h, nullptr, &n))) return rc;
+    std::vector<char> snap(n);
+    if ((rc = pt_checkpoint(h, snap.data(), &n))) return rc;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(h, cudaEventCreate(&a));
+    CK(h, cudaEventCreate(&b));
+    int best = h->variant;
+    float best_ms = 1e30f;
+    const int variants[] = {kSweepSimple, kSweepLookahead, kSweepTeam, kSweepWpm};
+    for (int v : variants) {
+        if ((rc = pt_set_sweep_kernel(h, v))) break;
+        if ((rc = pt_sweep(h, 2, 1))) break;  // warm-up (and graph capture)
+        CK(h, cudaEventRecord(a, h->stream));
+        if ((rc = pt_sweep(h, trial_sweeps, 1))) break;
+        CK(h, cudaEventRecord(b, h->stream));
+        if ((rc = sync_and_check(h))) break;
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+        if ((rc = pt_restore(h, snap.data(), snap.size()))) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc;
+    if ((rc = pt_set_sweep_kernel(h, best))) return rc;
+    if ((rc = pt_restore(h, snap.data(), snap.size()))) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = best;
+        tune_store(h->gpu_name, h->nmax, h->G, best);
+    }
+    if (chosen) *chosen = best;
+    return PT_OK;
+}
+
+extern "C" int pt_get_sweep_kernel(const pt_ctx* h) { return h ? h->variant : -1; }
 
 extern "C" int pt_set_kernel_timing(pt_ctx* h, int on) {
     int rc = check_usable(h);

@@ -63,22 +63,25 @@ __device__ __forceinline__ void sweep_epilogue(const State& S, const EnsDev& ed,
         E = full;
     }
     if (lane == 0) {
+        // Fire-and-forget atomic adds (no value returned, so the warp does not wait on L2).
+        // The slot has a single writer until the next exchange and one thread's adds to an
+        // address apply in program order, so the sums are deterministic.
         if (!isfinite(E)) {
             atomicOr(S.err, kErrNonFinite);
         } else if (s >= ed.n_therm) {
             if (E < ed.e_min) {
-                S.outl[2 * gs] += 1.0;
+                atomicAdd(&S.outl[2 * gs], 1.0);
             } else {
                 const double b = floor((E - ed.e_min) * ed.inv_w);
-                if (b >= (double)ed.n_bins) S.outl[2 * gs + 1] += 1.0;
-                else S.hist[ed.hist_base + (int64_t)slot * ed.n_bins + (int64_t)b] += 1.0;
+                if (b >= (double)ed.n_bins) atomicAdd(&S.outl[2 * gs + 1], 1.0);
+                else atomicAdd(&S.hist[ed.hist_base + (int64_t)slot * ed.n_bins + (int64_t)b], 1.0);
             }
-            S.mom[3 * gs] += 1.0;
-            S.mom[3 * gs + 1] += E;
-            S.mom[3 * gs + 2] += E * E;
+            atomicAdd(&S.mom[3 * gs], 1.0);
+            atomicAdd(&S.mom[3 * gs + 1], E);
+            atomicAdd(&S.mom[3 * gs + 2], E * E);
         }
-        S.mv_att[gs] += (unsigned long long)N;
-        S.mv_acc[gs] += (unsigned long long)nacc;
+        atomicAdd(&S.mv_att[gs], (unsigned long long)N);
+        atomicAdd(&S.mv_acc[gs], (unsigned long long)nacc);
         if (logging) S.log_e[(size_t)(s - S.log_s0) * S.n_reps + g] = E;
     }
 }

@@ -68,6 +68,8 @@ _SIGS = {
     "pt_energy_fp64": (_I, [_V, _V, _I, _I, _I, _V]),
     "pt_energy_fp64_noalloc": (_I, [_V, _I, _I, _I, _V, _V]),
     "pt_set_sweep_kernel": (_I, [_V, _I]),
+    "pt_get_sweep_kernel": (_I, [_V]),
+    "pt_autotune": (_I, [_V, _I, _I, ctypes.POINTER(ctypes.c_int)]),
     "pt_set_kernel_timing": (_I, [_V, _I]),
     "pt_kernel_timing": (_I, [_V, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "pt_checkpoint": (_I, [_V, _V, ctypes.POINTER(ctypes.c_size_t)]),
@@ -274,8 +276,19 @@ def pt_energy_fp64_noalloc(conf_dev_ptr: int, N: int, n_conf: int, lj_bonded: in
 
 
 def pt_set_sweep_kernel(h, variant: int) -> None:
-    """0: one move at a time (default); 1: lookahead groups of moves."""
+    """0 warp per replica, 1 lookahead groups, 2 team of warps, 3 warp per move of a group."""
     _ck(lib().pt_set_sweep_kernel(h, int(variant)))
+
+
+def pt_get_sweep_kernel(h) -> int:
+    return lib().pt_get_sweep_kernel(h)
+
+
+def pt_autotune(h, trial_sweeps: int = 8, force: bool = False) -> int:
+    """Time every sweep kernel on h (state restored afterwards) and keep the fastest."""
+    v = ctypes.c_int(-1)
+    _ck(lib().pt_autotune(h, int(trial_sweeps), int(bool(force)), ctypes.byref(v)))
+    return v.value
 
 
 def pt_set_kernel_timing(h, on: bool) -> None:

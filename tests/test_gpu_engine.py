@@ -199,3 +199,46 @@ def test_library_coil_is_valid():
             assert E[r] == pytest.approx(oracle.full_energy(x[r].astype(np.float32)), rel=1e-12, abs=1e-10)
     finally:
         pt.pt_destroy(h)
+
+
+def test_autotune_leaves_the_state_untouched():
+    h = _make(N=60, R=8, seed=9)
+    try:
+        pt.pt_sweep(h, 5, 1)
+        before = _state(h)
+        c0 = pt.pt_counters(h)
+        v = pt.pt_autotune(h, 4, force=True)
+        assert v in (0, 1, 2, 3) and pt.pt_get_sweep_kernel(h) == v
+        _same(_state(h), before)
+        assert pt.pt_counters(h) == c0
+        assert pt.pt_autotune(h, 4) == v  # cached
+        pt.pt_sweep(h, 5, 1)  # still runs after the restore
+        assert np.all(np.isfinite(pt.pt_energies(h)))
+    finally:
+        pt.pt_destroy(h)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_kernel_keeps_the_batch_bit_identical_to_separate_runs(variant):
+    """Per-ensemble results do not depend on which ensembles share the launch."""
+    specs = [(20, 4, 1, 0), (45, 7, 2, 1)]
+    made = [pt.make_params(N, inputs.temperature_ladder(0.2, 3.0, R), s, ensemble_id=e,
+                           init_positions=inputs.random_coil(N, R, s, e), n_bins=64)
+            for (N, R, s, e) in specs]
+    hb = pt.pt_create_batch([p for p, _ in made])
+    try:
+        pt.pt_set_sweep_kernel(hb, variant)
+        pt.pt_sweep(hb, 12, 1)
+        Pb = pt.pt_get_positions(hb)
+    finally:
+        pt.pt_destroy(hb)
+    po = 0
+    for (N, R, s, e), (p, _) in zip(specs, made):
+        h = pt.pt_create_ex(p)
+        try:
+            pt.pt_set_sweep_kernel(h, variant)
+            pt.pt_sweep(h, 12, 1)
+            assert np.array_equal(pt.pt_get_positions(h), Pb[po:po + 3 * R * N])
+        finally:
+            pt.pt_destroy(h)
+        po += 3 * R * N

@@ -211,6 +211,54 @@ int pt_kernel_timing(pt_ctx* h, double* mean_sweep_ms, int* n_launches);
 int pt_checkpoint(pt_ctx* h, void* buf, size_t* size);
 int pt_restore(pt_ctx* h, const void* buf, size_t size);
 
+/* ---- serving: continuous batching of PT jobs ----------------------------------------
+ * A server keeps one pool of device state (replica slots, beads, histogram bins, job
+ * descriptors). Submitted jobs wait until first-fit ranges of each kind are free (device
+ * memory admission, no head-of-line blocking), then run together: every scheduling round
+ * launches the sweep and exchange kernels once per sweep over the whole pool, and each job
+ * advances from its own sweep counter to its own budget. Finished jobs are copied to host
+ * memory and their ranges reused. A job's result depends only on its own parameters (for
+ * a given N_max and kernel), so it is the same served alone and served in a mix. */
+typedef struct pt_server pt_server;
+
+typedef struct pt_server_config {
+    int32_t N_max;            /* longest chain a job may have (also sizes shared memory) */
+    int32_t replica_capacity; /* replica slots resident at once, all jobs together        */
+    int64_t bead_capacity;    /* beads resident at once (sum of N x replicas)             */
+    int64_t hist_capacity;    /* histogram bins resident at once (sum of replicas x bins) */
+    int32_t job_capacity;     /* jobs resident at once                                    */
+    int32_t round_sweeps;     /* sweeps per scheduling round (64)                         */
+    int32_t threaded;         /* 1: a host thread runs the rounds; 0: pt_server_step      */
+    int32_t sweep_kernel;     /* -1: chosen from N_max; else as pt_set_sweep_kernel       */
+} pt_server_config;
+
+/* Capacities for jobs of up to N_max beads in mem_budget_bytes of device memory. */
+void pt_server_config_init(pt_server_config* c, int N_max, size_t mem_budget_bytes);
+pt_server* pt_server_create(const pt_server_config* c, void* stream);
+
+/* Queue a job (parameters copied; temperatures / init_positions read now). Returns a job
+ * id > 0, or a negative pt_status. n_sweeps and exchange_every as in pt_sweep. */
+int64_t pt_server_submit(pt_server* s, const pt_params* p, int64_t n_sweeps, int exchange_every);
+
+/* Unthreaded servers: run one round (admit, sweep, retire). Returns resident jobs or < 0. */
+int pt_server_step(pt_server* s);
+
+/* 2 queued, 1 running, 0 done, < 0 error. pt_server_wait blocks (runs rounds itself when
+ * unthreaded) until the job is done or timeout_s passes (PT_ETIMEOUT). */
+int pt_server_poll(pt_server* s, int64_t job);
+int pt_server_wait(pt_server* s, int64_t job, double timeout_s);
+
+/* Results of a finished job, then forgotten: energies by temperature slot [R], histograms
+ * [R][n_bins], moments [R][3] (count, sum E, sum E^2), and the submit-to-done latency in
+ * seconds. Any pointer may be NULL. PT_EBUSY if not finished. */
+int pt_server_result(pt_server* s, int64_t job, double* energies, double* hist, double* moments,
+                     double* latency_s);
+
+/* Jobs queued / running / done and single-bead updates done so far. */
+int pt_server_stats(pt_server* s, int64_t* queued, int64_t* running, int64_t* done, double* updates);
+
+void pt_server_destroy(pt_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -439,6 +439,19 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     return h;
 }
 
+}  // namespace
+
+namespace ptgb {
+// Shared with the job server (pt_server.cu).
+int default_sweep_variant(int nmax) { return default_variant(nmax); }
+void make_start_coil(float* out, int N, uint64_t seed, uint32_t ens_id, uint32_t rep) {
+    make_coil(out, N, seed, ens_id, rep);
+}
+bool chain_bonds_ok(const float* xyz, int N) { return bonds_ok(xyz, N); }
+}  // namespace ptgb
+
+namespace {
+
 template <class T>
 int copy_out(pt_ctx* h, T* out, const T* dev, size_t n) {
     int rc = sync_and_check(h);

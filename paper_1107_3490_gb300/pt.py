@@ -37,6 +37,13 @@ class pt_params(ctypes.Structure):
                 ("init_positions", ctypes.POINTER(ctypes.c_float))]
 
 
+class pt_server_config(ctypes.Structure):
+    _fields_ = [("N_max", ctypes.c_int32), ("replica_capacity", ctypes.c_int32),
+                ("bead_capacity", ctypes.c_int64), ("hist_capacity", ctypes.c_int64),
+                ("job_capacity", ctypes.c_int32), ("round_sweeps", ctypes.c_int32),
+                ("threaded", ctypes.c_int32), ("sweep_kernel", ctypes.c_int32)]
+
+
 _lib = None
 _V, _I, _I64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
 _SIGS = {
@@ -72,6 +79,15 @@ _SIGS = {
     "pt_autotune": (_I, [_V, _I, _I, ctypes.POINTER(ctypes.c_int)]),
     "pt_set_kernel_timing": (_I, [_V, _I]),
     "pt_kernel_timing": (_I, [_V, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "pt_server_config_init": (None, [ctypes.POINTER(pt_server_config), _I, ctypes.c_size_t]),
+    "pt_server_create": (_V, [ctypes.POINTER(pt_server_config), _V]),
+    "pt_server_submit": (_I64, [_V, ctypes.POINTER(pt_params), _I64, _I]),
+    "pt_server_step": (_I, [_V]),
+    "pt_server_poll": (_I, [_V, _I64]),
+    "pt_server_wait": (_I, [_V, _I64, _D]),
+    "pt_server_result": (_I, [_V, _I64, _V, _V, _V, ctypes.POINTER(ctypes.c_double)]),
+    "pt_server_stats": (_I, [_V, _V, _V, _V, ctypes.POINTER(ctypes.c_double)]),
+    "pt_server_destroy": (None, [_V]),
     "pt_checkpoint": (_I, [_V, _V, ctypes.POINTER(ctypes.c_size_t)]),
     "pt_restore": (_I, [_V, _V, ctypes.c_size_t]),
 }
@@ -399,3 +415,64 @@ class Ensemble:
                 self.close()
         except Exception:
             pass
+
+
+# ---- job server ------------------------------------------------------------------------
+def pt_server_config_init(N_max: int, mem_budget_bytes: int) -> pt_server_config:
+    c = pt_server_config()
+    lib().pt_server_config_init(ctypes.byref(c), int(N_max), int(mem_budget_bytes))
+    return c
+
+
+def pt_server_create(cfg: pt_server_config, stream=None):
+    s = lib().pt_server_create(ctypes.byref(cfg), stream)
+    if not s:
+        raise PtError(PT_EINVAL, pt_last_error())
+    return s
+
+
+def pt_server_submit(s, params: pt_params, n_sweeps: int, exchange_every: int = 1) -> int:
+    j = lib().pt_server_submit(s, ctypes.byref(params), int(n_sweeps), int(exchange_every))
+    if j < 0:
+        raise PtError(int(j), pt_last_error())
+    return j
+
+
+def pt_server_step(s) -> int:
+    r = lib().pt_server_step(s)
+    if r < 0:
+        raise PtError(r, pt_last_error())
+    return r
+
+
+def pt_server_poll(s, job: int) -> int:
+    return lib().pt_server_poll(s, int(job))
+
+
+def pt_server_wait(s, job: int, timeout_s: float = 600.0) -> int:
+    r = lib().pt_server_wait(s, int(job), float(timeout_s))
+    if r < 0:
+        raise PtError(r, pt_last_error())
+    return r
+
+
+def pt_server_result(s, job: int, n_replicas: int, n_bins: int):
+    """(energies [R], histograms [R, n_bins], moments [R, 3], latency seconds)."""
+    e = np.zeros(n_replicas)
+    h = np.zeros((n_replicas, n_bins))
+    m = np.zeros((n_replicas, 3))
+    lat = ctypes.c_double()
+    _ck(lib().pt_server_result(s, int(job), _p(e), _p(h), _p(m), ctypes.byref(lat)))
+    return e, h, m, lat.value
+
+
+def pt_server_stats(s):
+    q, r, d = (ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64())
+    u = ctypes.c_double()
+    rc = lib().pt_server_stats(s, ctypes.byref(q), ctypes.byref(r), ctypes.byref(d), ctypes.byref(u))
+    return dict(queued=q.value, running=r.value, done=d.value, updates=u.value, status=rc)
+
+
+def pt_server_destroy(s) -> None:
+    if s:
+        lib().pt_server_destroy(s)

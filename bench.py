@@ -289,12 +289,130 @@ def run_gpu(args):
     return 0
 
 
+def _timed(fn):
+    t0 = time.perf_counter()
+    fn()
+    return time.perf_counter() - t0
+
+
+def run_batched(args):
+    """256 uneven ensembles (N log-uniform 20-500, 8-64 replicas, T 0.2-3.0) in one context
+    with one set of launches, against the plain form (each ensemble its own context, swept
+    one after another) on the first ensembles."""
+    import torch
+    from paper_1107_3490_gb300 import inputs, pt
+    specs = inputs.batched_ensembles(256, n_sweeps=5000)
+    made = [pt.make_params(sp.n_beads, sp.temperatures(), sp.seed, ensemble_id=sp.ensemble_id, n_bins=1024)
+            for sp in specs]
+    steps_sweeps = 100
+    h = pt.pt_create_batch([p for p, _ in made])
+    kernel = pt.pt_autotune(h, 4)
+    for _ in range(args.warmup):
+        pt.pt_sweep(h, steps_sweeps, 1)
+    pt.pt_sync(h)
+    upd = sum(sp.n_beads * sp.n_replicas for sp in specs) * steps_sweeps
+    def timed_steps():
+        for _ in range(args.steps):
+            pt.pt_sweep(h, steps_sweeps, 1)
+        pt.pt_sync(h)
+
+    dt = _timed(timed_steps)
+    pt.pt_destroy(h)
+    value = upd * args.steps / dt
+    # plain form on a sample: one ensemble per context and per launch sequence
+    sample = specs[:16]
+    ctxs = []
+    for sp, (p, _) in zip(sample, made[:16]):
+        c = pt.pt_create_ex(p)
+        pt.pt_autotune(c, 4)
+        pt.pt_sweep(c, 10, 1)
+        ctxs.append(c)
+    for c in ctxs:
+        pt.pt_sync(c)
+    t = 0.0
+    for c in ctxs:
+        t += _timed(lambda: (pt.pt_sweep(c, steps_sweeps, 1), pt.pt_sync(c)))
+    plain = sum(sp.n_beads * sp.n_replicas for sp in sample) * steps_sweeps / t
+    for c in ctxs:
+        pt.pt_destroy(c)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "256 uneven PT ensembles: N log-uniform 20-500, replicas uniform 8-64, "
+                                   "T geometric 0.2-3.0, exchange every sweep; one step = 100 sweeps of all",
+                       "sweep_kernel": KERNEL_NAMES[kernel], "replicas": sum(sp.n_replicas for sp in specs)},
+            "plain_one_ensemble_per_launch": {"value": plain, "unit": UNIT, "sample": "first 16 ensembles, sequential"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served(args):
+    """A Poisson stream of PT jobs (N log-uniform 20-1000, 16-128 replicas, budgets
+    log-uniform 100-1000 sweeps) through the continuous-batching server, against running
+    the same jobs one after another as plain contexts (on a sample)."""
+    import threading
+    from paper_1107_3490_gb300 import inputs, pt
+    n_jobs = args.jobs
+    jobs = inputs.served_jobs(n_jobs, s_lo=100, s_hi=1000, rate_hz=args.rate)
+    # clients arrive with their start conformations ready (made before the clock starts)
+    made = [pt.make_params(j.n_beads, j.temperatures(), j.seed, ensemble_id=j.ensemble_id, n_bins=1024,
+                           init_positions=pt.pt_make_coil(j.n_beads, j.n_replicas, j.seed, j.ensemble_id))
+            for j in jobs]
+    cfg = pt.pt_server_config_init(1000, 6 << 30)
+    cfg.round_sweeps = 32
+    srv = pt.pt_server_create(cfg)
+    ids = [0] * n_jobs
+    t_start = time.perf_counter()
+
+    def feeder():
+        for i, (j, (p, _)) in enumerate(zip(jobs, made)):
+            delay = j.arrival_s - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            ids[i] = pt.pt_server_submit(srv, p, j.n_sweeps, 1)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    lat = []
+    for i, j in zip(ids, jobs):
+        pt.pt_server_wait(srv, i, 3600.0)
+        lat.append(pt.pt_server_result(srv, i, j.n_replicas, 1024)[3])
+    makespan = time.perf_counter() - t_start
+    upd = sum(j.n_beads * j.n_replicas * j.n_sweeps for j in jobs)
+    pt.pt_server_destroy(srv)
+    # plain form: the first jobs one after another, each its own context
+    sample = list(zip(jobs, made))[:8]
+    t = 0.0
+    for j, (p, _) in sample:
+        c = pt.pt_create_ex(p)
+        pt.pt_autotune(c, 4)
+        t += _timed(lambda: (pt.pt_sweep(c, j.n_sweeps, 1), pt.pt_sync(c)))
+        pt.pt_destroy(c)
+    plain = sum(j.n_beads * j.n_replicas * j.n_sweeps for j, _ in sample) / t
+    lat = sorted(lat)
+    line = {"metric": METRIC, "value": upd / makespan, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": f"{n_jobs} PT jobs, Poisson arrivals {args.rate}/s, N log-uniform 20-1000, "
+                                   "replicas uniform 16-128, budgets log-uniform 100-1000 sweeps, exchange every "
+                                   "sweep; server N_max 1000", "sweep_kernel": "k_sweep_wpm (chosen from N_max)"},
+            "latency_s": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                          "max": lat[-1]},
+            "makespan_s": makespan,
+            "plain_one_job_per_context": {"value": plain, "unit": UNIT, "sample": "first 8 jobs, sequential"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", choices=["plain", "batched", "served"], default="plain",
+                    help="plain: the benchmark line; batched / served: the uneven-ensemble and job-stream forms")
+    ap.add_argument("--jobs", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=40.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                     help="sweep kernel: -1 autotune (default), 0 warp per replica, 1 lookahead groups, "
@@ -306,6 +424,10 @@ def main(argv=None):
         return run_reference(args)
     from paper_1107_3490_gb300 import build
     build.build()
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_gpu(args)
 
 

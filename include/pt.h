@@ -68,6 +68,11 @@ typedef struct pt_params {
 void pt_params_init(pt_params* p, int N, int n_replicas, const double* temperatures,
                     uint64_t seed);
 
+/* The library's start conformations, host only (no GPU needed): for each replica a
+ * random-walk coil with every bond at r0 = 0.7 and every non-bonded distance >= r0,
+ * centred, written to out [n_replicas][N][3]. Used when init_positions is NULL. */
+int pt_make_coil(int N, int n_replicas, uint64_t seed, uint32_t ensemble_id, float* out);
+
 /* ---- the core calls --------------------------------------------------------------- */
 
 /* One ensemble with default parameters (Sec. 3). Returns NULL on error (see

@@ -464,6 +464,13 @@ int copy_out(pt_ctx* h, T* out, const T* dev, size_t n) {
 
 extern "C" {
 
+int pt_make_coil(int N, int n_replicas, uint64_t seed, uint32_t ensemble_id, float* out) {
+    if (N < 2 || N > PT_MAX_N || n_replicas < 1 || !out || ensemble_id >= (1u << 24))
+        return fail(PT_EINVAL, "pt_make_coil: bad arguments");
+    for (int r = 0; r < n_replicas; ++r) make_coil(out + 3 * (size_t)r * N, N, seed, ensemble_id, (uint32_t)r);
+    return PT_OK;
+}
+
 void pt_params_init(pt_params* p, int N, int n_replicas, const double* temperatures, uint64_t seed) {
     if (!p) return;
     std::memset(p, 0, sizeof *p);

@@ -1,16 +1,18 @@
 // pt_server.cu -- continuous batching of parallel-tempering jobs.
 //
-// The server owns one pool of device state with fixed capacities (replica slots, beads,
-// histogram bins, ensemble descriptors) sized from a memory budget. A submitted job waits
-// in a queue until first-fit ranges of every kind are free; it is then admitted: its
-// descriptors, start conformations and labels are written into its ranges and its FP64
-// energies computed. Every round launches the sweep and exchange kernels over the whole
-// pool, one sweep per launch pair; each replica advances from its own sweep counter to its
-// job's budget, so jobs admitted at different times progress together and a finished job
-// costs nothing until its slots are reused. After a round, finished jobs are copied out
-// (energies by temperature slot, histograms, moments) and their ranges freed, which lets
-// queued jobs in. A job's arithmetic depends only on its own descriptors and data, so its
-// result is the same alone and in any mix served with the same kernel.
+// The server keeps device state in pools, one per chain-length class (up to 64 beads, up to
+// 256, up to N_max), each with fixed capacities (replica slots, beads, histogram bins, job
+// descriptors), its own sweep kernel shape and its own CUDA stream, so the classes run
+// concurrently on the device. A submitted job waits in a queue until first-fit ranges of
+// every kind are free in its class's pool; it is then admitted: its descriptors, start
+// conformations and labels are written into its ranges and its FP64 energies computed.
+// Every round launches, per pool, the sweep and exchange kernels once per sweep over the
+// occupied part of the pool (up to its high-water mark); each replica advances from its own
+// sweep counter to its job's budget, so jobs admitted at different times progress together.
+// After a round, finished jobs are copied out (energies by temperature slot, histograms,
+// moments) and their ranges freed, which lets queued jobs in. A job's arithmetic depends
+// only on its own descriptors and data and on its pool's kernel, so its result is the same
+// served alone and in any mix.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -18,6 +20,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -27,7 +30,6 @@
 
 namespace ptgb {
 int set_error(int code, const char* msg);       // pt_api.cu
-int default_sweep_variant(int nmax);            // pt_api.cu
 void make_start_coil(float* out, int N, uint64_t seed, uint32_t ens_id, uint32_t rep);  // pt_api.cu
 bool chain_bonds_ok(const float* xyz, int N);   // pt_api.cu
 }  // namespace ptgb
@@ -38,11 +40,12 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-// First-fit allocator over [0, capacity).
+// First-fit allocator over [0, capacity); keeps used ranges packed at low indices.
 struct Ranges {
     std::map<int64_t, int64_t> free;  // start -> length
-    explicit Ranges(int64_t cap = 0) {
-        if (cap > 0) free[0] = cap;
+    int64_t cap = 0;
+    explicit Ranges(int64_t c = 0) : cap(c) {
+        if (c > 0) free[0] = c;
     }
     int64_t take(int64_t n) {
         for (auto it = free.begin(); it != free.end(); ++it)
@@ -69,17 +72,32 @@ struct Ranges {
             }
         }
     }
+    // one past the last used index
+    int64_t high() const {
+        if (free.empty()) return cap;
+        auto last = std::prev(free.end());
+        return last->first + last->second == cap ? last->first : cap;
+    }
+};
+
+struct Pool {
+    int nmax = 0, variant = 0, warps = 1, dummy = 0, n_jobs = 0;
+    State S{};
+    Ranges reps, beads, bins;
+    std::vector<int> free_ens;
+    int ens_high = 0;  // one past the highest ensemble slot in use
+    cudaStream_t stream = nullptr;
 };
 
 struct Job {
     int64_t id = 0;
     pt_params p{};
     std::vector<double> T;
-    std::vector<float> x0;  // empty: library coil
+    std::vector<float> x0;  // start conformations [R][N][3]
     int64_t n_sweeps = 0, done = 0;
     int exchange_every = 1;
     int status = 2;  // 2 queued, 1 running, 0 done, < 0 error
-    int e = -1;      // ensemble slot
+    int pool = -1, e = -1;
     int64_t rb = -1, pb = -1, hb = -1;
     Clock::time_point submitted, finished;
     std::vector<double> energies, hist, moments;
@@ -89,12 +107,8 @@ struct Job {
 
 struct pt_server {
     pt_server_config cfg{};
-    State S{};
-    int variant = 0, warps = 1, num_sms = 152;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    Ranges reps, beads, bins;
-    std::vector<int> free_ens;
+    int num_sms = 152;
+    std::vector<std::unique_ptr<Pool>> pools;  // by chain-length class
     std::map<int64_t, Job> jobs;
     std::deque<int64_t> queue;
     std::vector<int64_t> running;
@@ -105,7 +119,6 @@ struct pt_server {
     std::thread worker;
     bool stop = false;
     int error = 0;
-    int dummy_ens = 0;
 };
 
 namespace {
@@ -119,59 +132,107 @@ cudaError_t dzero(T** p, size_t n) {
     return e;
 }
 
-void free_pool(pt_server* s) {
-    State& S = s->S;
+void free_pool(Pool& P) {
+    State& S = P.S;
     void* ptrs[] = {S.reps, S.ens, S.pos, S.E, S.temp_of_rep, S.rep_of_temp, S.Tf, S.beta, S.hist,
                     S.outl, S.mom, S.mv_att, S.mv_acc, S.ex_att, S.ex_acc, S.drift, S.rep_sweep, S.err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     S = State{};
+    if (P.stream) cudaStreamDestroy(P.stream);
+    P.stream = nullptr;
 }
 
-// Write an inactive descriptor set: every replica slot points at the dummy ensemble, whose
-// target is 0, so the kernels return at once for it.
-cudaError_t reset_slots(pt_server* s, int64_t rb, int64_t n) {
+// Inactive slots point at the pool's dummy descriptor, whose sweep target is 0.
+cudaError_t reset_slots(Pool& P, int64_t rb, int64_t n) {
     std::vector<RepDev> rd((size_t)n);
     for (auto& r : rd) {
         r = RepDev{};
-        r.ens = s->dummy_ens;
+        r.ens = P.dummy;
         r.N = 2;
     }
-    return cudaMemcpy(s->S.reps + rb, rd.data(), n * sizeof(RepDev), cudaMemcpyHostToDevice);
+    return cudaMemcpy(P.S.reps + rb, rd.data(), n * sizeof(RepDev), cudaMemcpyHostToDevice);
 }
 
-void release(pt_server* s, Job& j);
+cudaError_t make_pool(Pool& P, int nmax, int64_t reps, int64_t beads, int64_t bins, int jobs, int variant, int num_sms) {
+    P.nmax = nmax;
+    State& S = P.S;
+    const size_t G = (size_t)reps, NE = (size_t)jobs + 1;
+    P.dummy = jobs;
+    S.n_reps = 0;
+    S.n_ens = 0;
+    S.nmax = nmax;
+    cudaError_t a = cudaStreamCreateWithFlags(&P.stream, cudaStreamNonBlocking);
+    auto A = [&](cudaError_t x) { if (a == cudaSuccess) a = x; };
+    A(dzero(&S.reps, G));
+    A(dzero(&S.ens, NE));
+    A(dzero(&S.pos, (size_t)beads));
+    A(dzero(&S.E, G));
+    A(dzero(&S.temp_of_rep, G));
+    A(dzero(&S.rep_of_temp, G));
+    A(dzero(&S.Tf, G));
+    A(dzero(&S.beta, G));
+    A(dzero(&S.hist, (size_t)bins));
+    A(dzero(&S.outl, 2 * G));
+    A(dzero(&S.mom, 3 * G));
+    A(dzero(&S.mv_att, G));
+    A(dzero(&S.mv_acc, G));
+    A(dzero(&S.ex_att, G));
+    A(dzero(&S.ex_acc, G));
+    A(dzero(&S.drift, G));
+    A(dzero(&S.rep_sweep, G));
+    A(dzero(&S.err, 1));
+    if (a == cudaSuccess) a = reset_slots(P, 0, (int64_t)G);
+    P.reps = Ranges(reps);
+    P.beads = Ranges(beads);
+    P.bins = Ranges(bins);
+    for (int e = jobs - 1; e >= 0; --e) P.free_ens.push_back(e);
+    // short chains: one warp per replica; longer: warp per move of a group
+    P.variant = variant >= 0 ? variant : (nmax <= 64 ? kSweepSimple : kSweepWpm);
+    P.warps = sweep_warps_per_block(nmax, (int)G, num_sms, P.variant);
+    if (a == cudaSuccess) a = configure_sweep(nmax, P.warps, P.variant);
+    return a;
+}
 
+void release(Pool& P, Job& j) {
+    const int R = j.p.n_replicas, N = j.p.N;
+    reset_slots(P, j.rb, R);
+    EnsDev d{};
+    cudaMemcpy(P.S.ens + j.e, &d, sizeof d, cudaMemcpyHostToDevice);
+    P.reps.give(j.rb, R);
+    P.beads.give(j.pb, (int64_t)N * R);
+    P.bins.give(j.hb, (int64_t)R * j.p.n_bins);
+    P.free_ens.push_back(j.e);
+    --P.n_jobs;
+}
+
+// 1 admitted, 0 no room yet, -2 rejected (non-finite start energy), -1 CUDA failure.
 int admit(pt_server* s, Job& j) {
+    Pool& P = *s->pools[j.pool];
     const pt_params& p = j.p;
     const int R = p.n_replicas, N = p.N;
-    const int64_t rb = s->reps.take(R);
+    if (P.free_ens.empty()) return 0;
+    const int64_t rb = P.reps.take(R);
     if (rb < 0) return 0;
-    const int64_t pb = s->beads.take((int64_t)N * R);
+    const int64_t pb = P.beads.take((int64_t)N * R);
     if (pb < 0) {
-        s->reps.give(rb, R);
+        P.reps.give(rb, R);
         return 0;
     }
-    const int64_t hb = s->bins.take((int64_t)R * p.n_bins);
+    const int64_t hb = P.bins.take((int64_t)R * p.n_bins);
     if (hb < 0) {
-        s->reps.give(rb, R);
-        s->beads.give(pb, (int64_t)N * R);
+        P.reps.give(rb, R);
+        P.beads.give(pb, (int64_t)N * R);
         return 0;
     }
-    if (s->free_ens.empty()) {
-        s->reps.give(rb, R);
-        s->beads.give(pb, (int64_t)N * R);
-        s->bins.give(hb, (int64_t)R * p.n_bins);
-        return 0;
-    }
-    const int e = s->free_ens.back();
-    s->free_ens.pop_back();
+    const int e = P.free_ens.back();
+    P.free_ens.pop_back();
+    ++P.n_jobs;
     j.e = e;
     j.rb = rb;
     j.pb = pb;
     j.hb = hb;
-    State& S = s->S;
-    // descriptors
+    State& S = P.S;
     std::vector<RepDev> rd(R);
     for (int r = 0; r < R; ++r) {
         rd[r] = RepDev{};
@@ -197,7 +258,6 @@ int admit(pt_server* s, Job& j) {
     d.recompute_every = p.recompute_every;
     d.n_therm = p.n_therm;
     d.target = j.n_sweeps;
-    // labels, temperatures, start conformations
     std::vector<int32_t> ident(R);
     std::vector<float> Tf(R);
     std::vector<double> beta(R);
@@ -207,27 +267,15 @@ int admit(pt_server* s, Job& j) {
         beta[t] = 1.0 / j.T[t];
     }
     std::vector<float4> x4((size_t)N * R);
-    std::vector<float> coil(3 * (size_t)N);
-    for (int r = 0; r < R; ++r) {
-        const float* src = nullptr;
-        if (!j.x0.empty()) {
-            src = j.x0.data() + 3 * (size_t)r * N;
-        } else {
-            make_start_coil(coil.data(), N, p.seed, p.ensemble_id, (uint32_t)r);
-            src = coil.data();
-        }
-        for (int i = 0; i < N; ++i)
-            x4[(size_t)r * N + i] = make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.f);
-    }
-    cudaError_t c = cudaMemcpy(S.reps + rb, rd.data(), R * sizeof(RepDev), cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.ens + e, &d, sizeof d, cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.temp_of_rep + rb, ident.data(), R * 4, cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.rep_of_temp + rb, ident.data(), R * 4, cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.Tf + rb, Tf.data(), R * 4, cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.beta + rb, beta.data(), R * 8, cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.pos + pb, x4.data(), x4.size() * sizeof(float4), cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemset(S.hist + hb, 0, (size_t)R * p.n_bins * 8);
+    for (size_t i = 0; i < x4.size(); ++i) x4[i] = make_float4(j.x0[3 * i], j.x0[3 * i + 1], j.x0[3 * i + 2], 0.f);
     const size_t RR = (size_t)R;
+    cudaError_t c = cudaMemcpy(S.reps + rb, rd.data(), RR * sizeof(RepDev), cudaMemcpyHostToDevice);
+    if (c == cudaSuccess) c = cudaMemcpy(S.ens + e, &d, sizeof d, cudaMemcpyHostToDevice);
+    if (c == cudaSuccess) c = cudaMemcpy(S.temp_of_rep + rb, ident.data(), RR * 4, cudaMemcpyHostToDevice);
+    if (c == cudaSuccess) c = cudaMemcpy(S.rep_of_temp + rb, ident.data(), RR * 4, cudaMemcpyHostToDevice);
+    if (c == cudaSuccess) c = cudaMemcpy(S.Tf + rb, Tf.data(), RR * 4, cudaMemcpyHostToDevice);
+    if (c == cudaSuccess) c = cudaMemcpy(S.beta + rb, beta.data(), RR * 8, cudaMemcpyHostToDevice);
+    if (c == cudaSuccess) c = cudaMemcpy(S.pos + pb, x4.data(), x4.size() * sizeof(float4), cudaMemcpyHostToDevice);
     if (c == cudaSuccess) c = cudaMemset(S.outl + 2 * rb, 0, 2 * RR * 8);
     if (c == cudaSuccess) c = cudaMemset(S.mom + 3 * rb, 0, 3 * RR * 8);
     if (c == cudaSuccess) c = cudaMemset(S.mv_att + rb, 0, RR * 8);
@@ -236,50 +284,35 @@ int admit(pt_server* s, Job& j) {
     if (c == cudaSuccess) c = cudaMemset(S.ex_acc + rb, 0, RR * 8);
     if (c == cudaSuccess) c = cudaMemset(S.drift + rb, 0, RR * 8);
     if (c == cudaSuccess) c = cudaMemset(S.rep_sweep + rb, 0, RR * 8);
-    // FP64 start energies (Eq. 4); scratch for the partial sums lives in the job's
-    // histogram range until the job starts measuring
+    // FP64 start energies (Eq. 4); the partial sums use the job's histogram range as
+    // scratch before it is cleared (submit checks it is large enough)
     const int nc = energy_chunks(N);
-    double* scratch = S.hist + hb;
-    if ((size_t)R * p.n_bins < (size_t)R * nc) scratch = nullptr;
-    if (c == cudaSuccess && scratch)
-        c = launch_energy(S.pos, S.reps + rb, S.ens, 0, 1, R, S.E + rb, scratch, nc, s->stream);
-    if (c == cudaSuccess && scratch) c = cudaStreamSynchronize(s->stream);
-    if (c == cudaSuccess && scratch) c = cudaMemsetAsync(S.hist + hb, 0, (size_t)R * p.n_bins * 8, s->stream);
-    if (c == cudaSuccess) c = cudaStreamSynchronize(s->stream);
-    if (c != cudaSuccess || !scratch) {
-        s->error = PT_ECUDA;
-        return -1;
-    }
+    if (c == cudaSuccess)
+        c = launch_energy(S.pos, S.reps + rb, S.ens, 0, 1, R, S.E + rb, S.hist + hb, nc, P.stream);
+    if (c == cudaSuccess) c = cudaStreamSynchronize(P.stream);
+    if (c == cudaSuccess) c = cudaMemset(S.hist + hb, 0, RR * p.n_bins * 8);
     std::vector<double> E(R);
-    if (cudaMemcpy(E.data(), S.E + rb, R * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (c == cudaSuccess) c = cudaMemcpy(E.data(), S.E + rb, RR * 8, cudaMemcpyDeviceToHost);
+    if (c != cudaSuccess) {
         s->error = PT_ECUDA;
         return -1;
     }
     for (double v : E)
         if (!std::isfinite(v)) {
             j.status = PT_EINVAL;  // overlapping start conformation
-            release(s, j);
+            release(P, j);
             return -2;
         }
+    P.S.n_reps = (int)std::max<int64_t>(P.S.n_reps, rb + R);
+    P.ens_high = std::max(P.ens_high, e + 1);
+    P.S.n_ens = P.ens_high;
     j.status = 1;
     return 1;
 }
 
-void release(pt_server* s, Job& j) {
-    const int R = j.p.n_replicas, N = j.p.N;
-    reset_slots(s, j.rb, R);
-    EnsDev d{};
-    d.rep_base = 0;
-    cudaMemcpy(s->S.ens + j.e, &d, sizeof d, cudaMemcpyHostToDevice);
-    s->reps.give(j.rb, R);
-    s->beads.give(j.pb, (int64_t)N * R);
-    s->bins.give(j.hb, (int64_t)R * j.p.n_bins);
-    s->free_ens.push_back(j.e);
-}
-
-int collect(pt_server* s, Job& j) {
+int collect(Pool& P, Job& j) {
     const int R = j.p.n_replicas;
-    State& S = s->S;
+    State& S = P.S;
     std::vector<double> E(R);
     std::vector<int32_t> rot(R);
     j.hist.resize((size_t)R * j.p.n_bins);
@@ -294,10 +327,11 @@ int collect(pt_server* s, Job& j) {
     return PT_OK;
 }
 
-// One scheduling round; the caller holds s->mu.
-int round_locked(pt_server* s) {
+// One scheduling round. The caller holds s->mu through lk; it is released while the GPU
+// works, so submissions and polls never wait for a round (only this thread touches the
+// pools, and the job table is read and written under the lock).
+int round_locked(pt_server* s, std::unique_lock<std::mutex>& lk) {
     if (s->error) return s->error;
-    // admit in queue order, skipping jobs that do not fit yet
     for (auto it = s->queue.begin(); it != s->queue.end();) {
         Job& j = s->jobs[*it];
         const int a = admit(s, j);
@@ -320,36 +354,47 @@ int round_locked(pt_server* s) {
         todo = std::max(todo, j.n_sweeps - j.done);
     }
     const int64_t n = std::min<int64_t>(todo, s->cfg.round_sweeps);
-    for (int64_t i = 0; i < n; ++i) {
-        cudaError_t c = launch_sweep(s->S, 1, s->warps, s->variant, s->stream);
-        if (c == cudaSuccess) c = launch_exchange(s->S, s->stream);
-        if (c != cudaSuccess) {
-            s->error = PT_ECUDA;
-            return s->error;
+    const std::vector<int64_t> batch = s->running;
+    lk.unlock();
+    // every pool with jobs on its own stream: the classes overlap on the device
+    int gpu_err = 0;
+    for (auto& pp : s->pools) {
+        Pool& P = *pp;
+        if (P.n_jobs == 0) continue;
+        for (int64_t i = 0; i < n && !gpu_err; ++i) {
+            cudaError_t c = launch_sweep(P.S, 1, P.warps, P.variant, P.stream);
+            if (c == cudaSuccess) c = launch_exchange(P.S, P.stream);
+            if (c != cudaSuccess) gpu_err = PT_ECUDA;
         }
     }
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
-        s->error = PT_ECUDA;
-        return s->error;
+    for (auto& pp : s->pools) {
+        Pool& P = *pp;
+        if (P.n_jobs == 0 || gpu_err) continue;
+        int err = 0;
+        if (cudaStreamSynchronize(P.stream) != cudaSuccess ||
+            cudaMemcpy(&err, P.S.err, sizeof err, cudaMemcpyDeviceToHost) != cudaSuccess)
+            gpu_err = PT_ECUDA;
+        else if (err & kErrNonFinite)
+            gpu_err = PT_ESTATE;
     }
-    int err = 0;
-    cudaMemcpy(&err, s->S.err, sizeof err, cudaMemcpyDeviceToHost);
-    if (err & kErrNonFinite) {
-        s->error = PT_ESTATE;
+    lk.lock();
+    if (gpu_err) {
+        s->error = gpu_err;
         return s->error;
     }
     std::vector<int64_t> still;
-    for (int64_t id : s->running) {
+    for (int64_t id : batch) {
         Job& j = s->jobs[id];
         const int64_t adv = std::min(n, j.n_sweeps - j.done);
         j.done += adv;
         s->updates += (double)adv * j.p.N * j.p.n_replicas;
         if (j.done >= j.n_sweeps) {
-            if (collect(s, j)) {
+            Pool& P = *s->pools[j.pool];
+            if (collect(P, j)) {
                 s->error = PT_ECUDA;
                 return s->error;
             }
-            release(s, j);
+            release(P, j);
             j.status = 0;
             j.finished = Clock::now();
             ++s->n_done;
@@ -358,6 +403,15 @@ int round_locked(pt_server* s) {
         }
     }
     s->running.swap(still);
+    // shrink the launched ranges to what is still occupied
+    for (auto& pp : s->pools) {
+        Pool& P = *pp;
+        P.S.n_reps = (int)P.reps.high();
+        while (P.ens_high > 0 &&
+               std::find(P.free_ens.begin(), P.free_ens.end(), P.ens_high - 1) != P.free_ens.end())
+            --P.ens_high;
+        P.S.n_ens = P.ens_high;
+    }
     s->cv.notify_all();
     return (int)s->running.size();
 }
@@ -369,11 +423,20 @@ void worker_loop(pt_server* s) {
             s->cv.wait(lk);
             continue;
         }
-        if (round_locked(s) < 0) {
+        if (round_locked(s, lk) < 0) {
             s->cv.notify_all();
             s->cv.wait(lk, [s] { return s->stop; });
         }
     }
+}
+
+// Chain-length classes: (lower bound exclusive, upper bound inclusive].
+constexpr int kClassTop[] = {64, 256, PT_MAX_N};
+
+int pool_of(const pt_server* s, int N) {
+    for (size_t i = 0; i < s->pools.size(); ++i)
+        if (N <= s->pools[i]->nmax) return (int)i;
+    return -1;
 }
 
 }  // namespace
@@ -385,93 +448,63 @@ void pt_server_config_init(pt_server_config* c, int N_max, size_t mem_budget_byt
     std::memset(c, 0, sizeof *c);
     if (N_max < 2) N_max = 2;
     c->N_max = N_max;
-    // worst case per replica: N_max beads (16 B), 4096 FP64 bins, per-replica state
-    const size_t per_rep = (size_t)N_max * 16 + 4096 * 8 + 256;
+    // per replica: about N_max / 4 beads on average (16 B), 4096 FP64 bins, state
+    const size_t per_rep = (size_t)std::max(16, N_max / 4) * 16 + 4096 * 8 + 256;
     int64_t reps = (int64_t)(mem_budget_bytes / per_rep);
     reps = std::max<int64_t>(2, std::min<int64_t>(reps, 1 << 20));
     c->replica_capacity = (int32_t)reps;
-    c->bead_capacity = reps * N_max;
+    c->bead_capacity = reps * std::max(16, N_max / 4);
     c->hist_capacity = reps * 4096;
-    c->job_capacity = (int32_t)std::min<int64_t>(4096, std::max<int64_t>(1, reps / 2));
+    c->job_capacity = (int32_t)std::min<int64_t>(4096, std::max<int64_t>(1, reps / 4));
     c->round_sweeps = 64;
     c->threaded = 1;
     c->sweep_kernel = -1;
 }
 
 pt_server* pt_server_create(const pt_server_config* c, void* stream) {
+    (void)stream;  // every pool has its own stream
     if (!c || c->N_max < 2 || c->N_max > PT_MAX_N || c->replica_capacity < 1 || c->bead_capacity < 2 ||
         c->hist_capacity < 1 || c->job_capacity < 1 || c->round_sweeps < 1) {
         set_error(PT_EINVAL, "pt_server_create: bad configuration");
         return nullptr;
     }
-    if ((int64_t)c->replica_capacity + 1 > 0x7fffffff || c->bead_capacity > 0x7fffffff) {
-        set_error(PT_EINVAL, "pt_server_create: capacity too large");
+    if (c->bead_capacity > 0x7fffffff) {
+        set_error(PT_EINVAL, "pt_server_create: bead capacity too large");
         return nullptr;
     }
     pt_server* s = new pt_server();
     s->cfg = *c;
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) {
-        if (stream) {
-            s->stream = (cudaStream_t)stream;
-        } else {
-            e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-            s->own_stream = e == cudaSuccess;
-        }
-    }
-    if (e != cudaSuccess) {
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         set_error(PT_ECUDA, "pt_server_create: no usable CUDA device");
         delete s;
         return nullptr;
     }
-    State& S = s->S;
-    const size_t G = (size_t)c->replica_capacity, NE = (size_t)c->job_capacity + 1;
-    s->dummy_ens = c->job_capacity;
-    S.n_reps = (int)G;
-    S.n_ens = (int)NE;
-    S.nmax = c->N_max;
-    cudaError_t a = cudaSuccess;
-    auto A = [&](cudaError_t x) { if (a == cudaSuccess) a = x; };
-    A(dzero(&S.reps, G));
-    A(dzero(&S.ens, NE));
-    A(dzero(&S.pos, (size_t)c->bead_capacity));
-    A(dzero(&S.E, G));
-    A(dzero(&S.temp_of_rep, G));
-    A(dzero(&S.rep_of_temp, G));
-    A(dzero(&S.Tf, G));
-    A(dzero(&S.beta, G));
-    A(dzero(&S.hist, (size_t)c->hist_capacity));
-    A(dzero(&S.outl, 2 * G));
-    A(dzero(&S.mom, 3 * G));
-    A(dzero(&S.mv_att, G));
-    A(dzero(&S.mv_acc, G));
-    A(dzero(&S.ex_att, G));
-    A(dzero(&S.ex_acc, G));
-    A(dzero(&S.drift, G));
-    A(dzero(&S.rep_sweep, G));
-    A(dzero(&S.err, 1));
-    if (a == cudaSuccess) a = reset_slots(s, 0, (int64_t)G);
-    if (a != cudaSuccess) {
-        set_error(a == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA, "pt_server_create: device allocation");
-        free_pool(s);
-        if (s->own_stream) cudaStreamDestroy(s->stream);
-        delete s;
-        return nullptr;
+    // pools for the classes up to N_max; capacities split evenly in replicas and bins,
+    // beads in proportion to each class's longest chain
+    std::vector<int> tops;
+    for (int t : kClassTop) {
+        tops.push_back(std::min(t, c->N_max));
+        if (t >= c->N_max) break;
     }
-    s->reps = Ranges(c->replica_capacity);
-    s->beads = Ranges(c->bead_capacity);
-    s->bins = Ranges(c->hist_capacity);
-    for (int e2 = c->job_capacity - 1; e2 >= 0; --e2) s->free_ens.push_back(e2);
-    s->variant = c->sweep_kernel >= 0 ? c->sweep_kernel : default_sweep_variant(c->N_max);
-    s->warps = sweep_warps_per_block(c->N_max, (int)G, s->num_sms, s->variant);
-    if (configure_sweep(c->N_max, s->warps, s->variant) != cudaSuccess) {
-        set_error(PT_ECUDA, "pt_server_create: configure sweep kernel");
-        free_pool(s);
-        if (s->own_stream) cudaStreamDestroy(s->stream);
-        delete s;
-        return nullptr;
+    const int np = (int)tops.size();
+    int64_t wsum = 0;
+    for (int t : tops) wsum += t;
+    for (int i = 0; i < np; ++i) {
+        auto P = std::make_unique<Pool>();
+        const int64_t reps = std::max<int64_t>(2, c->replica_capacity / np);
+        const int64_t beads = std::max<int64_t>((int64_t)tops[i] * 2, c->bead_capacity * tops[i] / wsum);
+        const int64_t bins = std::max<int64_t>(64, c->hist_capacity / np);
+        const int jobs = std::max(1, c->job_capacity / np);
+        if (make_pool(*P, tops[i], reps, beads, bins, jobs, c->sweep_kernel, s->num_sms) != cudaSuccess) {
+            set_error(PT_ENOMEM, "pt_server_create: device allocation");
+            for (auto& q : s->pools) free_pool(*q);
+            free_pool(*P);
+            delete s;
+            return nullptr;
+        }
+        s->pools.push_back(std::move(P));
     }
     if (c->threaded) s->worker = std::thread(worker_loop, s);
     return s;
@@ -482,9 +515,11 @@ int64_t pt_server_submit(pt_server* s, const pt_params* p, int64_t n_sweeps, int
     if (!p || p->N < 2 || p->N > s->cfg.N_max || p->n_replicas < 1 || !p->temperatures || n_sweeps < 0 ||
         exchange_every < 0 || p->n_bins < 1 || !(p->e_max > p->e_min) || p->ensemble_id >= (1u << 24))
         return set_error(PT_EINVAL, "pt_server_submit: bad job parameters (N must be <= the server's N_max)");
-    if (p->n_replicas > s->cfg.replica_capacity || (int64_t)p->N * p->n_replicas > s->cfg.bead_capacity ||
-        (int64_t)p->n_replicas * p->n_bins > s->cfg.hist_capacity || p->n_bins < energy_chunks(p->N))
-        return set_error(PT_EINVAL, "pt_server_submit: job larger than the server's capacity");
+    const int pi = pool_of(s, p->N);
+    const Pool& P = *s->pools[pi];
+    if (p->n_replicas > P.reps.cap || (int64_t)p->N * p->n_replicas > P.beads.cap ||
+        (int64_t)p->n_replicas * p->n_bins > P.bins.cap || p->n_bins < energy_chunks(p->N))
+        return set_error(PT_EINVAL, "pt_server_submit: job larger than the server's capacity for its chain length");
     for (int t = 0; t < p->n_replicas; ++t)
         if (!(std::isfinite(p->temperatures[t]) && p->temperatures[t] > 0))
             return set_error(PT_EINVAL, "pt_server_submit: temperatures must be finite and > 0");
@@ -497,10 +532,17 @@ int64_t pt_server_submit(pt_server* s, const pt_params* p, int64_t n_sweeps, int
         for (int r = 0; r < p->n_replicas; ++r)
             if (!chain_bonds_ok(j.x0.data() + 3 * (size_t)r * p->N, p->N))
                 return set_error(PT_EINVAL, "pt_server_submit: start conformation with a broken bond");
+    } else {
+        // the library's start coils are made here, in the submitting thread, so that the
+        // scheduling loop never waits for host work
+        j.x0.resize(3 * (size_t)p->N * p->n_replicas);
+        for (int r = 0; r < p->n_replicas; ++r)
+            make_start_coil(j.x0.data() + 3 * (size_t)r * p->N, p->N, p->seed, p->ensemble_id, (uint32_t)r);
     }
     j.p.init_positions = nullptr;
     j.n_sweeps = n_sweeps;
     j.exchange_every = exchange_every;
+    j.pool = pi;
     j.submitted = Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->error) return set_error(s->error, "server failed earlier");
@@ -515,8 +557,8 @@ int64_t pt_server_submit(pt_server* s, const pt_params* p, int64_t n_sweeps, int
 int pt_server_step(pt_server* s) {
     if (!s) return set_error(PT_EINVAL, "null server");
     if (s->cfg.threaded) return set_error(PT_EINVAL, "pt_server_step: the server runs its own thread");
-    std::lock_guard<std::mutex> lk(s->mu);
-    const int r = round_locked(s);
+    std::unique_lock<std::mutex> lk(s->mu);
+    const int r = round_locked(s, lk);
     return r < 0 ? set_error(r, "server round failed") : r;
 }
 
@@ -537,8 +579,7 @@ int pt_server_wait(pt_server* s, int64_t job, double timeout_s) {
     const auto until = Clock::now() + std::chrono::duration<double>(std::max(0.0, timeout_s));
     while (it->second.status > 0 && !s->error) {
         if (!s->cfg.threaded) {
-            const int r = round_locked(s);
-            if (r < 0) break;
+            if (round_locked(s, lk) < 0) break;
             continue;
         }
         if (s->cv.wait_until(lk, until) == std::cv_status::timeout) return set_error(PT_ETIMEOUT, "job not finished");
@@ -585,9 +626,10 @@ void pt_server_destroy(pt_server* s) {
         s->cv.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
-    cudaStreamSynchronize(s->stream);
-    free_pool(s);
-    if (s->own_stream) cudaStreamDestroy(s->stream);
+    for (auto& P : s->pools) {
+        if (P->stream) cudaStreamSynchronize(P->stream);
+        free_pool(*P);
+    }
     delete s;
 }
 

@@ -48,6 +48,7 @@ _lib = None
 _V, _I, _I64, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
 _SIGS = {
     "pt_params_init": (None, [ctypes.POINTER(pt_params), _I, _I, _V, ctypes.c_uint64]),
+    "pt_make_coil": (_I, [_I, _I, ctypes.c_uint64, ctypes.c_uint32, _V]),
     "pt_create": (_V, [_I, _I, _V, ctypes.c_uint64]),
     "pt_create_ex": (_V, [ctypes.POINTER(pt_params), _V]),
     "pt_create_batch": (_V, [_I, ctypes.POINTER(pt_params), _V]),
@@ -128,6 +129,13 @@ def pt_params_init(N, n_replicas, temperatures, seed) -> tuple[pt_params, np.nda
     p = pt_params()
     lib().pt_params_init(ctypes.byref(p), int(N), int(n_replicas), _p(T), int(seed))
     return p, T
+
+
+def pt_make_coil(N: int, n_replicas: int, seed: int, ensemble_id: int = 0) -> np.ndarray:
+    """The library's default start coils [n_replicas, N, 3] (host only)."""
+    out = np.zeros((int(n_replicas), int(N), 3), dtype=np.float32)
+    _ck(lib().pt_make_coil(int(N), int(n_replicas), int(seed), int(ensemble_id), _p(out)))
+    return out
 
 
 def pt_create(N, n_replicas, temperatures, seed):

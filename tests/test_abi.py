@@ -54,3 +54,18 @@ def test_calls_without_gpu_fail_cleanly():
     with pytest.raises(pt.PtError):
         pt.pt_create(10, 2, [0.5, 1.0], 1)
     assert pt.pt_last_error()
+
+
+def test_library_start_coils_without_gpu():
+    """pt_make_coil is host-only: bonds at r0, non-bonded distances >= r0, deterministic."""
+    import numpy as np
+    from paper_1107_3490_gb300 import pt
+    _lib_path()
+    a = pt.pt_make_coil(60, 3, 11, 2).astype(np.float64)
+    b = pt.pt_make_coil(60, 3, 11, 2).astype(np.float64)
+    assert np.array_equal(a, b)
+    bonds = np.linalg.norm(a[:, 1:] - a[:, :-1], axis=2)
+    assert np.all(np.abs(bonds - 0.7) < 1e-5)
+    for r in range(3):
+        d = np.linalg.norm(a[r, :, None] - a[r, None, :], axis=2)
+        assert d[np.triu_indices(60, 2)].min() >= 0.7 - 1e-5

@@ -50,7 +50,7 @@ def test_served_alone_equals_served_in_a_mix():
     assert mixed[1].sum() == 8 * 200
 
 
-def test_served_job_matches_a_standalone_context_within_tolerance():
+def test_served_job_matches_a_standalone_context():
     p, keep = _job(30, 8, 7, 7)
     s = pt.pt_server_create(_cfg())
     try:
@@ -61,14 +61,13 @@ def test_served_job_matches_a_standalone_context_within_tolerance():
         pt.pt_server_destroy(s)
     h = pt.pt_create_ex(p)
     try:
-        pt.pt_set_sweep_kernel(h, 3)
+        pt.pt_set_sweep_kernel(h, 0)  # the kernel of the server's class for chains up to 64 beads
         pt.pt_sweep(h, 100, 1)
         e_ctx, h_ctx = pt.pt_energies(h), pt.pt_histograms(h).reshape(8, 64)
     finally:
         pt.pt_destroy(h)
-    # same chain up to the summation order of dE (same kernel family and group width)
-    np.testing.assert_allclose(e_srv, e_ctx, rtol=0, atol=1e-3)
-    assert h_srv.sum() == h_ctx.sum() == 800
+    assert np.array_equal(e_srv, e_ctx) and np.array_equal(h_srv, h_ctx)
+    assert h_srv.sum() == 800
 
 
 def test_admission_waits_for_capacity_and_every_job_finishes():

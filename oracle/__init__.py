@@ -10,7 +10,8 @@ compiles it with gcc on first use and exposes it through ctypes:
 * potentials of Sec. 3.1 (Eqs. 1-3) and the total energy of Eq. 4;
 * the single-bead Metropolis move of Sec. 3.2 (Eq. 5) with Philox4x32-10 draws;
 * the neighbour exchange of Sec. 3.3 (Eq. 6);
-* the moments behind the specific heat of Sec. 4.1 (Eq. 7).
+* the moments behind the specific heat of Sec. 4.1 (Eq. 7) and the shape observables
+  r_gyr^2 (Eq. 8) and R_ee^2 with their fluctuation sums.
 
 ``OracleEnsemble`` runs one ensemble's chain step by step, optionally logging every move.
 """
@@ -62,7 +63,8 @@ class OrcState(ctypes.Structure):
                 ("check_fail", ctypes.c_int64), ("check_max", ctypes.c_double),
                 ("log_s0", ctypes.c_int64), ("log_ns", ctypes.c_int64),
                 ("log_bead", _P), ("log_de", _P), ("log_theta", _P), ("log_acc", _P),
-                ("log_e", _P), ("log_x", _P)]
+                ("log_e", _P), ("log_x", _P),
+                ("obs", _P), ("obs_rg2_hist", _P), ("obs_ree2_hist", _P)]
 
 
 def lib():
@@ -98,6 +100,8 @@ def lib():
         L.orc_cv_per_n.argtypes = [d, d, d, d, i]
         L.orc_rgyr2.restype = d
         L.orc_rgyr2.argtypes = [_P, i]
+        L.orc_ree2.restype = d
+        L.orc_ree2.argtypes = [_P, i]
         _lib = L
     return _lib
 
@@ -168,6 +172,11 @@ def rgyr2(pos) -> float:
     return lib().orc_rgyr2(_ptr(p), p.shape[0])
 
 
+def ree2(pos) -> float:
+    p = np.ascontiguousarray(pos, dtype=np.float32)
+    return lib().orc_ree2(_ptr(p), p.shape[0])
+
+
 # ---- one ensemble's chain --------------------------------------------------------------
 class OracleEnsemble:
     """State and run loop of one PT ensemble, mirroring the library's pt_params fields."""
@@ -202,9 +211,15 @@ class OracleEnsemble:
         self.ex_att = np.zeros(max(R - 1, 1), dtype=np.uint64)
         self.ex_acc = np.zeros(max(R - 1, 1), dtype=np.uint64)
         self.drift = np.zeros(R, dtype=np.float64)
+        # shape observables per slot: sum rg2, rg2^2, ree2, ree2^2, E rg2, E ree2, and the
+        # per-energy-bin sums of rg2 and ree2 (Sec. 4.1)
+        self.obs = np.zeros((R, 6), dtype=np.float64)
+        self.obs_rg2_hist = np.zeros((R, int(n_bins)), dtype=np.float64)
+        self.obs_ree2_hist = np.zeros((R, int(n_bins)), dtype=np.float64)
         self.st = OrcState()
         for name in ("pos", "E", "temp_of_rep", "rep_of_temp", "T", "hist", "outl", "mom",
-                     "mv_att", "mv_acc", "ex_att", "ex_acc", "drift"):
+                     "mv_att", "mv_acc", "ex_att", "ex_acc", "drift", "obs", "obs_rg2_hist",
+                     "obs_ree2_hist"):
             setattr(self.st, name, _ptr(getattr(self, name)))
         self.log = None
 

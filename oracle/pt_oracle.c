@@ -213,7 +213,14 @@ typedef struct {
     uint8_t* log_acc;     /* [log_ns][R][N]                                           */
     double* log_e;        /* [log_ns][R] energy after the moves (and recompute)       */
     int8_t* log_x;        /* [log_ns][R] outcome of pair (t,t+1): -1 none, 0 no, 1 swap */
+    /* optional shape observables (Sec. 4.1), per temperature slot; NULL = off            */
+    double* obs;          /* [R][6] sum rg2, rg2^2, ree2, ree2^2, E rg2, E ree2        */
+    double* obs_rg2_hist; /* [R][n_bins] sum of rg2 over the samples of each energy bin */
+    double* obs_ree2_hist;/* [R][n_bins] sum of ree2 over the samples of each bin      */
 } orc_state;
+
+double orc_rgyr2(const float* pos, int N);
+double orc_ree2(const float* pos, int N);
 
 /* One exchange round (Sec. 3.3, Eq. 6) over the pairs of parity xround % 2.
  * Accept iff u < exp[(E_t - E_{t+1}) (beta_t - beta_{t+1})], all in FP64. */
@@ -333,18 +340,36 @@ int orc_run(const orc_params* p, orc_state* st, int64_t n_sweeps, int64_t exchan
                 int t = st->temp_of_rep[r];
                 double e = st->E[r];
                 double x = (e - p->e_min) * inv_w;
+                int64_t bin = -1;
                 if (e < p->e_min) {
                     st->outl[2 * t] += 1.0;
                 } else {
                     double b = floor(x);
-                    if (b >= (double)p->n_bins)
+                    if (b >= (double)p->n_bins) {
                         st->outl[2 * t + 1] += 1.0;
-                    else
+                    } else {
+                        bin = (int64_t)b;
                         st->hist[(size_t)t * p->n_bins + (size_t)b] += 1.0;
+                    }
                 }
                 st->mom[3 * t] += 1.0;
                 st->mom[3 * t + 1] += e;
                 st->mom[3 * t + 2] += e * e;
+                if (st->obs) {
+                    const float* pr = st->pos + (size_t)r * N * 3;
+                    double g2 = orc_rgyr2(pr, N), q2 = orc_ree2(pr, N);
+                    double* o = st->obs + 6 * (size_t)t;
+                    o[0] += g2;
+                    o[1] += g2 * g2;
+                    o[2] += q2;
+                    o[3] += q2 * q2;
+                    o[4] += e * g2;
+                    o[5] += e * q2;
+                    if (bin >= 0 && st->obs_rg2_hist) {
+                        st->obs_rg2_hist[(size_t)t * p->n_bins + (size_t)bin] += g2;
+                        st->obs_ree2_hist[(size_t)t * p->n_bins + (size_t)bin] += q2;
+                    }
+                }
             }
         }
         int8_t* xo = logging ? st->log_x + (size_t)(s - st->log_s0) * R : NULL;
@@ -363,6 +388,16 @@ int orc_run(const orc_params* p, orc_state* st, int64_t n_sweeps, int64_t exchan
 double orc_cv_per_n(double count, double sum_e, double sum_e2, double T, int N) {
     double m1 = sum_e / count, m2 = sum_e2 / count;
     return (m2 - m1 * m1) / (T * T) / (double)N;
+}
+
+/* Squared end-to-end distance |r_N - r_1|^2 of the chain (Sec. 4: measured per sweep). */
+double orc_ree2(const float* pos, int N) {
+    double s = 0;
+    for (int a = 0; a < 3; ++a) {
+        double d = (double)pos[3 * (N - 1) + a] - (double)pos[a];
+        s += d * d;
+    }
+    return s;
 }
 
 /* Eq. 8: r_gyr^2 = 1/N sum_k (r_k - r_mean)^2, r_mean the centre of mass. */

@@ -8,6 +8,8 @@ Sec. 3.1 (Eqs. 1-3) in numpy so that these references stay independent of the ch
   radial integral of r^2 exp(-beta V(r)) over the FENE window (r0 - R, r0 + R).
 * ``trimer_moments``: the N = 3 chain, integrated over (r12, r23, cos theta) with
   weight r12^2 r23^2 exp(-beta V); V holds the non-bonded 1-3 LJ term with its cutoff.
+* ``dimer_r2_moments`` / ``trimer_shape``: the same integrals for the shape observables
+  (R_ee^2, and r_gyr^2 of Eq. 8 through the pair identity, without a centre of mass).
 * ``exchange_*``: brute-force enumeration of the label permutations of a few frozen
   conformations and the exact transition matrix of one exchange round (Eq. 6).
 """
@@ -67,6 +69,24 @@ def dimer_moments(T: float, lj_bonded: int = 1):
     return m1, m2, beta * beta * (m2 - m1 * m1)
 
 
+def dimer_r2_moments(T: float, lj_bonded: int = 1):
+    """<r^2> and <r^4> of the dimer's bond length: R_ee^2 = r^2 and r_gyr^2 = r^2 / 4."""
+    beta = 1.0 / T
+    lo, hi = R0 - RF, R0 + RF
+    vmin = float(_bond(R0, lj_bonded))
+
+    def w(r, p):
+        v = float(_bond(r, lj_bonded))
+        if not np.isfinite(v):
+            return 0.0
+        return r * r * math.exp(-beta * (v - vmin)) * r ** p
+
+    kw = dict(limit=400, epsabs=0.0, epsrel=1e-12, points=[R0])
+    z = integrate.quad(lambda r: w(r, 0), lo, hi, **kw)[0]
+    return (integrate.quad(lambda r: w(r, 2), lo, hi, **kw)[0] / z,
+            integrate.quad(lambda r: w(r, 4), lo, hi, **kw)[0] / z)
+
+
 def trimer_moments(T: float, lj_bonded: int = 1, n_r: int = 80, n_c: int = 96):
     """<E>, <E^2> of the N = 3 chain by Gauss-Legendre quadrature over (r12, r23, cos).
 
@@ -93,6 +113,31 @@ def trimer_moments(T: float, lj_bonded: int = 1, n_r: int = 80, n_c: int = 96):
     m1 = np.sum(wgt * b * vz) / z
     m2 = np.sum(wgt * b * vz * vz) / z
     return float(m1), float(m2), float(beta * beta * (m2 - m1 * m1))
+
+
+def trimer_shape(T: float, lj_bonded: int = 1, n_r: int = 80, n_c: int = 96):
+    """<R_ee^2> = <r13^2> and <r_gyr^2> of the N = 3 chain, the latter through the pair
+    identity r_gyr^2 = (r12^2 + r23^2 + r13^2) / 9 (no centre of mass involved)."""
+    beta = 1.0 / T
+    xa, wa = np.polynomial.legendre.leggauss(n_r)
+    xs, ws = [], []
+    for a, b in ((R0 - RF, R0), (R0, R0 + RF)):
+        xs.append(0.5 * (b - a) * xa + 0.5 * (b + a))
+        ws.append(0.5 * (b - a) * wa)
+    r, wr = np.concatenate(xs), np.concatenate(ws)
+    xc, wc = np.polynomial.legendre.leggauss(n_c)
+    vb = _bond(r, lj_bonded)
+    r1, r2, c = np.meshgrid(r, r, xc, indexing="ij")
+    q13 = np.maximum(r1 * r1 + r2 * r2 - 2.0 * r1 * r2 * c, 1e-300)
+    v = vb[:, None, None] + vb[None, :, None] + v_lj_mod(np.sqrt(q13))
+    vmin = np.min(v[np.isfinite(v)])
+    wgt = (wr * r * r)[:, None, None] * (wr * r * r)[None, :, None] * wc[None, None, :]
+    with np.errstate(over="ignore", invalid="ignore"):
+        b = np.where(np.isfinite(v), np.exp(-beta * (v - vmin)), 0.0)
+    z = np.sum(wgt * b)
+    ree2 = np.sum(wgt * b * q13) / z
+    rg2 = np.sum(wgt * b * (r1 * r1 + r2 * r2 + q13)) / (9.0 * z)
+    return float(ree2), float(rg2)
 
 
 # ---- exchange step by enumeration (Eq. 6) -----------------------------------------------

@@ -184,12 +184,17 @@ int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonde
 int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, double* out,
                            void* stream);
 
-/* Choose the sweep kernel: 0 = one warp per replica, one move at a time (default);
+/* Choose the sweep kernel (creation picks 0 below 50 beads, 4 up to 250, else 3):
+ * 0 = one warp per replica, one move at a time;
  * 1 = one warp per replica, groups of up to 8 consecutive moves with distinct beads
  * evaluated together; 2 = a CTA of 1-8 warps per replica (by N), one move at a time;
  * 3 = a CTA of 2-8 warps per replica, each warp evaluating one move of a group of moves with
- * distinct beads. All run the same chain, move for move; they differ only in the summation
- * order of dE. */
+ * distinct beads; 4 = one warp per replica with the chain in registers (N_max <= 1024),
+ * taking double-float work only where a decision or an accepted dE needs it. Kernels 0-3
+ * run the same chain, move for move, and differ only in the summation order of dE. Kernel
+ * 4 takes each Metropolis decision whose dE lies outside its FP32 error bound of theta
+ * exactly, so it runs that chain too except where a dE falls within the parity tolerance of
+ * its threshold. PT_EINVAL for an unknown kernel or kernel 4 with N_max > 1024. */
 int pt_set_sweep_kernel(pt_ctx* h, int variant);
 
 /* The kernel in use (creation picks one from the chain length; see pt_autotune). */
@@ -234,7 +239,8 @@ typedef struct pt_server_config {
     int32_t job_capacity;     /* jobs resident at once                                    */
     int32_t round_sweeps;     /* sweeps per scheduling round (64)                         */
     int32_t threaded;         /* 1: a host thread runs the rounds; 0: pt_server_step      */
-    int32_t sweep_kernel;     /* -1: chosen from N_max; else as pt_set_sweep_kernel       */
+    int32_t sweep_kernel;     /* -1: chosen from N_max; else as pt_set_sweep_kernel (4 on  */
+                              /* a class above 1024 beads runs kernel 3)                  */
 } pt_server_config;
 
 /* Capacities for jobs of up to N_max beads in mem_budget_bytes of device memory. */

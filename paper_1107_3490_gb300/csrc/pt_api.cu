@@ -265,7 +265,7 @@ void drop_graph(pt_ctx* h) {
 // Kernel choice before any tuning, from timings on GB300 (4 x 64 replicas up to N = 300,
 // 128 replicas above): one warp per replica wins for short chains, the warp-per-move
 // lookahead from about 50 beads on.
-int default_variant(int nmax) { return nmax < 50 ? kSweepSimple : kSweepWpm; }
+int default_variant(int nmax) { return nmax < 50 ? kSweepSimple : nmax <= 250 ? kSweepReg : kSweepWpm; }
 
 pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     g_err.clear();
@@ -620,8 +620,10 @@ extern "C" int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every) {
 extern "C" int pt_set_sweep_kernel(pt_ctx* h, int variant) {
     int rc = check_usable(h);
     if (rc) return rc;
-    if (variant < kSweepSimple || variant > kSweepWpm)
+    if (variant < kSweepSimple || variant > kSweepReg)
         return fail(PT_EINVAL, "unknown sweep kernel %d", variant);
+    if (variant == kSweepReg && h->nmax > kRegMaxN)
+        return fail(PT_EINVAL, "sweep kernel %d holds chains of at most %d beads", variant, kRegMaxN);
     if ((rc = sync_and_check(h))) return rc;
     const int warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, variant);
     CK(h, configure_sweep(h->nmax, warps, variant));
@@ -685,8 +687,9 @@ extern "C" int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen) 
     CK(h, cudaEventCreate(&b));
     int best = h->variant;
     float best_ms = 1e30f;
-    const int variants[] = {kSweepSimple, kSweepLookahead, kSweepTeam, kSweepWpm};
+    const int variants[] = {kSweepSimple, kSweepLookahead, kSweepTeam, kSweepWpm, kSweepReg};
     for (int v : variants) {
+        if (v == kSweepReg && h->nmax > kRegMaxN) continue;
         if ((rc = pt_set_sweep_kernel(h, v))) break;
         if ((rc = pt_sweep(h, 2, 1))) break;  // warm-up (and graph capture)
         CK(h, cudaEventRecord(a, h->stream));

@@ -1,0 +1,137 @@
+// pt_sweep.cuh -- pieces shared by the sweep kernels: warp reductions, the end-of-sweep
+// bookkeeping (FP64 recompute of Eq. 4, measurement, counters) and the FP32 / double-float
+// pair and bond terms of a single-bead move (Eqs. 1-3).
+#pragma once
+#include <cfloat>
+#include <cmath>
+
+#include "pt_device.cuh"
+#include "pt_internal.h"
+
+namespace ptgb {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int m = 16; m; m >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, m));
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(kFull, v, m);
+    return v;
+}
+
+// FP64 total energy of the chain in shared memory, computed by one warp (Eq. 4).
+static __device__ double warp_full_energy(const float4* P, int N, int lj_bonded, int lane) {
+    double e = 0.0;
+    for (int i = lane; i < N; i += 32) {
+        float4 pi = P[i];
+        for (int j = i + 1; j < N; ++j) {
+            double r2 = r2_d(pi, P[j]);
+            if (j == i + 1) {
+                e += fene_d(r2);
+                if (lj_bonded) e += lj_mod_d(r2);
+            } else {
+                e += lj_mod_d(r2);
+            }
+        }
+    }
+    return warp_sum_d(e);
+}
+
+
+// End of one sweep of replica g (all lanes of its warp call it): the periodic FP64
+// recompute of Eq. 4, then the measurement into the replica's temperature slot (the
+// replica owns the slot until the next exchange, so plain read-modify-write is race-free)
+// and the move counters.
+__device__ __forceinline__ void sweep_epilogue(const State& S, const EnsDev& ed, int g, int gs, int slot, int N,
+                                               const float4* P, int lane, int64_t s, int nacc, bool logging,
+                                               double& E) {
+    if (ed.recompute_every > 0 && (s + 1) % ed.recompute_every == 0) {
+        const double full = warp_full_energy(P, N, ed.lj_bonded, lane);
+        if (lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
+        E = full;
+    }
+    if (lane == 0) {
+        // Fire-and-forget atomic adds (no value returned, so the warp does not wait on L2).
+        // The slot has a single writer until the next exchange and one thread's adds to an
+        // address apply in program order, so the sums are deterministic.
+        if (!isfinite(E)) {
+            atomicOr(S.err, kErrNonFinite);
+        } else if (s >= ed.n_therm) {
+            if (E < ed.e_min) {
+                atomicAdd(&S.outl[2 * gs], 1.0);
+            } else {
+                const double b = floor((E - ed.e_min) * ed.inv_w);
+                if (b >= (double)ed.n_bins) atomicAdd(&S.outl[2 * gs + 1], 1.0);
+                else atomicAdd(&S.hist[ed.hist_base + (int64_t)slot * ed.n_bins + (int64_t)b], 1.0);
+            }
+            atomicAdd(&S.mom[3 * gs], 1.0);
+            atomicAdd(&S.mom[3 * gs + 1], E);
+            atomicAdd(&S.mom[3 * gs + 2], E * E);
+        }
+        atomicAdd(&S.mv_att[gs], (unsigned long long)N);
+        atomicAdd(&S.mv_acc[gs], (unsigned long long)nacc);
+        if (logging) S.log_e[(size_t)(s - S.log_s0) * S.n_reps + g] = E;
+    }
+}
+
+__device__ __forceinline__ float lj_term_f32(float r2o, float r2n) {
+    const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
+    const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
+    return __fmul_rn(__fsub_rn(xn, xo), __fmaf_rn(kAf, __fadd_rn(xn, xo), -kBf));
+}
+__device__ __forceinline__ float r2_f32(float4 q, float3 p) {
+    const float dx = __fsub_rn(q.x, p.x), dy = __fsub_rn(q.y, p.y), dz = __fsub_rn(q.z, p.z);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+// Double-float paths are rare; keeping them out of line keeps the hot loops small.
+static __device__ __noinline__ float lj_diff_df(float4 q, float3 p, float3 pn) {
+    return df_f(df_sub(lj_df(r2_df(q, pn)), lj_df(r2_df(q, p))));
+}
+static __device__ __noinline__ float bond_term_df(float4 q, float3 p, float3 pn, bool lj, bool lj_fast, float r2o, float r2n,
+                                          bool* broken) {
+    const df a = r2_df(q, p), b = r2_df(q, pn);
+    const float f = fene_diff_df(a, b);
+    if (isinf(f)) {
+        *broken = true;
+        return 0.f;
+    }
+    return lj ? __fadd_rn(f, lj_fast ? lj_term_f32(r2o, r2n) : df_f(df_sub(lj_df(b), lj_df(a)))) : f;
+}
+// Bonded partner q of the moved bead: FENE (Eq. 3) plus, if lj, the LJ term.
+__device__ __forceinline__ float bond_term_team(float4 q, float3 p, float3 pn, bool lj, bool* broken) {
+    const float r2o = r2_f32(q, p), r2n = r2_f32(q, pn);
+    const float uo = __fsub_rn(__fsqrt_rn(r2o), (float)kR0), un = __fsub_rn(__fsqrt_rn(r2n), (float)kR0);
+    const bool fene_fast = fmaxf(fabsf(uo), fabsf(un)) < kFeneUmaxF;
+    const bool lj_fast = fminf(r2o, r2n) >= kSteepTeam2f;
+    if (!fene_fast) return bond_term_df(q, p, pn, lj, lj_fast, r2o, r2n, broken);
+    float t = fene_diff_f32(q, p, pn, r2o, r2n);
+    if (lj) t = __fadd_rn(t, lj_fast ? lj_term_f32(r2o, r2n) : lj_diff_df(q, p, pn));
+    return t;
+}
+
+// Queued steep pairs of one warp, two lanes per pair (old and new side in parallel);
+// returns this lane's share (the even lane of each pair holds the difference).
+static __device__ __noinline__ df lj_side_df(float4 q, float3 x) { return lj_df(r2_df(q, x)); }
+__device__ __forceinline__ float steep_pairs(const int* Q, int qn, const float4* P, float3 p, float3 pn, int kf,
+                                             float4 pf, int lane) {
+    float acc = 0.f;
+    const int side = lane & 1;
+    for (int e0 = 0; e0 < qn; e0 += 16) {
+        const int e = e0 + (lane >> 1);
+        df v = {0.f, 0.f};
+        if (e < qn) {
+            const int j = Q[e];
+            const float4 q = j == kf ? pf : P[j];
+            v = lj_side_df(q, side ? pn : p);
+        }
+        const float nh = __shfl_sync(kFull, v.hi, lane | 1), nl = __shfl_sync(kFull, v.lo, lane | 1);
+        if (e < qn && side == 0) acc = __fadd_rn(acc, df_f(df_sub(df{nh, nl}, v)));
+    }
+    return acc;
+}
+
+}  // namespace ptgb

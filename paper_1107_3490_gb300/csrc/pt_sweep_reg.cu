@@ -1,0 +1,397 @@
+// pt_sweep_reg.cu -- warp-per-replica sweep with the energy row held in registers, the
+// Metropolis decision taken from an exact integer sum with a rigorous error bound, and the
+// double-float work deferred to the moves whose outcome or energy needs it.
+//
+// One warp owns one replica (Sec. 3.2). Lane l keeps beads l, l + 32, ... of the chain in
+// registers, so the O(N) row of a move (Eqs. 1-2) reads no memory; a shared-memory copy
+// serves the moved bead's own position and its bonds. Per batch of 32 moves the lanes make
+// the draws (one move per lane), the two bond terms of each move in FP32 against the
+// positions at batch start, and, per move, the set of earlier batch moves whose bead is the
+// same or bonded: if one of those was accepted, the move evaluates its bonds itself.
+//
+// Per move every lane forms, in FP32, its share of dE (row terms, steep pairs included, and
+// on lane 0 the bonds) and a bound on that share's rounding error:
+//  * pair term t = x_n (A x_n - B) - x_o (A x_o - B), x = r^-6: the relative error of x from
+//    the rounded coordinate differences and r^2, the approximate reciprocal and two products
+//    is at most 17 units of 2^-24 (2e-6 is used); it enters t through dt/dx = 2 A x - B;
+//  * bond (Eq. 3): the cancellation-free FENE difference -(K R^2/2) log1p((u_o^2 - u_n^2)/w_o)
+//    with a first-order bound through every rounded intermediate (w = R^2 - u^2, u = r - r0);
+//  * the summation inside a lane adds (U + 3) 2^-24 sum |t|.
+// Each lane's share minus / plus its bound, rounded down / up to 2^-16, goes through an exact
+// fixed-point integer warp sum (redux.sync), which brackets the exact dE. A decision with
+// theta outside that bracket is the one exact arithmetic takes, and a rejected move's dE is
+// used nowhere.
+// An accepted move needs its dE (it enters the FP64 energy): a float butterfly sum, or, if
+// the move has a steep pair or a bond far from r0 (|r - r0| >= 0.2), the double-float
+// evaluation of those terms exactly as the other sweep kernels do for every move. A move
+// inside the bracket takes that value and decides on it, like the other kernels. With the
+// per-move log on, every move computes the value it logs in the same way.
+#include "pt_sweep.cuh"
+
+namespace ptgb {
+
+namespace {
+
+constexpr float kEps0 = 5.9604645e-08f;  // 2^-24
+constexpr float kDeltaX = 2.0e-6f;       // bound on the relative error of x = r^-6 in FP32
+constexpr float kFar = 1.0e18f;          // coordinate of an absent partner (r^2 stays finite)
+constexpr float kQ = 65536.f;            // fixed point of the decision sums: 2^-16 per unit
+constexpr float kQInv = 1.52587890625e-05f;
+constexpr float kQMax = 1000.f;          // lane bounds clamped to +-1000: 32 lanes fit in int32
+constexpr float kEdge = 1.0e-5f;         // bond lengths this close to the FENE wall: undecided
+
+// Bonded partner q of the moved bead in FP32: FENE (Eq. 3) plus, if lj, the LJ term, with a
+// bound e on the rounding error. inexact: the accurate value needs double-float (a bond
+// length at least 0.2 from r0, or a steep LJ term); edge: a bond length within kEdge of the
+// FENE wall, where FP32 cannot tell whether the bond breaks.
+struct BondF {
+    float t, e;
+    bool inexact, edge;
+};
+__device__ __forceinline__ BondF bond_f32(float4 q, float3 p, float3 pn, bool lj) {
+    const float R = (float)kRF;
+    BondF b = {0.f, 0.f, false, false};
+    const float r2o = r2_f32(q, p), r2n = r2_f32(q, pn);
+    const float ro = __fsqrt_rn(r2o), rn = __fsqrt_rn(r2n);
+    const float uo = __fsub_rn(ro, (float)kR0), un = __fsub_rn(rn, (float)kR0);
+    if (fabsf(un) > R + kEdge) {  // the bond breaks: E = +inf, the move is rejected
+        b.t = __int_as_float(0x7f800000);
+        return b;
+    }
+    const float umax = fmaxf(fabsf(uo), fabsf(un));
+    if (umax >= R - kEdge) {
+        b.edge = true;
+        return b;
+    }
+    b.inexact = umax >= kFeneUmaxF;
+    const float tf = fene_diff_f32(q, p, pn, r2o, r2n);
+    // first-order bound through the intermediates of fene_diff_f32 (same expressions)
+    const float dx = __fsub_rn(pn.x, p.x), dy = __fsub_rn(pn.y, p.y), dz = __fsub_rn(pn.z, p.z);
+    const float sx = __fsub_rn(__fmul_rn(2.f, __fsub_rn(q.x, p.x)), dx);
+    const float sy = __fsub_rn(__fmul_rn(2.f, __fsub_rn(q.y, p.y)), dy);
+    const float sz = __fsub_rn(__fmul_rn(2.f, __fsub_rn(q.z, p.z)), dz);
+    const float e_dr2 = 8.f * kEps0 * (fabsf(dx * sx) + fabsf(dy * sy) + fabsf(dz * sz) + dx * dx + dy * dy + dz * dz);
+    const float rsum = __fadd_rn(ro, rn);
+    const float drr = __fdividef(__fmaf_rn(dz, sz, __fmaf_rn(dy, sy, __fmul_rn(dx, sx))), rsum);
+    const float usum = __fadd_rn(uo, un);
+    const float wo = __fmul_rn(__fsub_rn(R, uo), __fadd_rn(R, uo));
+    const float z = __fdividef(__fmul_rn(drr, usum), wo);
+    const float e_u = 3.0e-7f;  // |r| error (rounded r^2 and sqrt) plus the float rounding of r0
+    const float e_drr = e_dr2 / rsum + fabsf(drr) * (2.f * e_u / rsum + 4.f * kEps0);
+    const float e_wo = 2.f * R * (e_u + 2.e-8f) + 4.f * kEps0 * wo;
+    const float e_z = (e_drr * fabsf(usum) + fabsf(drr) * (2.f * e_u + kEps0)) / wo + fabsf(z) * (e_wo / wo + 4.f * kEps0);
+    const float den = 1.f + z - e_z;
+    if (!(den > 0.05f)) {  // log1p too steep here for this simple bound
+        b.edge = true;
+        return b;
+    }
+    float e = 1.5f * (1.8f * e_z / den + 4.f * kEps0 * fabsf(tf)) + 1e-9f;
+    float t = tf;
+    if (lj) {
+        const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
+        const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
+        const float tl = lj_term_f32(r2o, r2n);
+        const float w = fabsf(xo * (2.f * kAf * xo - kBf)) + fabsf(xn * (2.f * kAf * xn - kBf));
+        e += kDeltaX * w + 4.f * kEps0 * fabsf(tl);
+        b.inexact |= fminf(r2o, r2n) < kSteepTeam2f;
+        t = __fadd_rn(t, tl);
+    }
+    b.t = t;
+    b.e = e + kEps0 * fabsf(t);
+    return b;
+}
+
+}  // namespace
+
+// Row of the moved bead k over this lane's partners: sums of the ordinary and of the steep
+// FP32 terms, of |t| and of the error weights |x_o (2 A x_o - B)| + |x_n (2 A x_n - B)|, and
+// the mask of slots holding a steep partner. Slot u holds bead lane + 32 u. Slots go in
+// groups of four without a branch inside a group, so that their dependency chains
+// interleave; a group wholly beyond N is skipped.
+struct RowSums {
+    float aord, ast, sab, sw;
+    unsigned stm;
+};
+template <int U>
+__device__ __forceinline__ RowSums row_pass(const float (&qx)[U], const float (&qy)[U], const float (&qz)[U],
+                                            float3 p, float3 pn, int k, int lane, int N) {
+    RowSums r = {0.f, 0.f, 0.f, 0.f, 0u};
+    const int kk = lane - k + 1;  // j - k + 1 for slot 0
+#pragma unroll
+    for (int u0 = 0; u0 < U; u0 += 4) {
+        if (u0 > 0 && 32 * u0 >= N) break;
+#pragma unroll
+        for (int u = u0; u < u0 + 4 && u < U; ++u) {
+            const float dxo = __fsub_rn(qx[u], p.x), dyo = __fsub_rn(qy[u], p.y), dzo = __fsub_rn(qz[u], p.z);
+            const float dxn = __fsub_rn(qx[u], pn.x), dyn = __fsub_rn(qy[u], pn.y), dzn = __fsub_rn(qz[u], pn.z);
+            const float r2o = __fmaf_rn(dzo, dzo, __fmaf_rn(dyo, dyo, __fmul_rn(dxo, dxo)));
+            const float r2n = __fmaf_rn(dzn, dzn, __fmaf_rn(dyn, dyn, __fmul_rn(dxn, dxn)));
+            const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
+            const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
+            const float t = __fmul_rn(__fsub_rn(xn, xo), __fmaf_rn(kAf, __fadd_rn(xn, xo), -kBf));
+            const float w = __fadd_rn(fabsf(__fmul_rn(__fmaf_rn(2.f * kAf, xo, -kBf), xo)),
+                                      fabsf(__fmul_rn(__fmaf_rn(2.f * kAf, xn, -kBf), xn)));
+            const bool use = (unsigned)(kk + 32 * u) > 2u;  // neither k nor bonded to k
+            const bool st = use && fminf(r2o, r2n) < kSteepTeam2f;
+            r.aord = __fadd_rn(r.aord, (use && !st) ? t : 0.f);
+            r.ast = __fadd_rn(r.ast, st ? t : 0.f);
+            r.sab = __fadd_rn(r.sab, use ? fabsf(t) : 0.f);
+            r.sw = __fadd_rn(r.sw, use ? w : 0.f);
+            r.stm |= st ? (1u << u) : 0u;
+        }
+    }
+    return r;
+}
+
+template <int U>
+__global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
+    extern __shared__ float4 smem[];
+    const int lane = threadIdx.x;
+    const int g = blockIdx.x;
+    if (g >= S.n_reps) return;
+    const RepDev rd = S.reps[g];
+    const EnsDev ed = S.ens[rd.ens];
+    const int N = rd.N;
+    int64_t s = S.rep_sweep[g];
+    const int64_t s_end = min(ed.target, s + (int64_t)chunk);
+    if (s >= s_end) return;
+
+    float4* P = smem;                                  // [nmax] the chain
+    float4* D0 = P + S.nmax;                           // [32] move: bead | bond flags << 16, displacement
+    float4* D1 = D0 + 32;                              // [32] move: theta, bond terms, bound, conflicts
+    int* Q = reinterpret_cast<int*>(D1 + 32);          // [nmax] steep partners of a refined move
+    float qx[U], qy[U], qz[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int j = lane + 32 * u;
+        float4 q = make_float4(kFar, kFar, kFar, 0.f);
+        if (j < N) {
+            q = S.pos[rd.pos_off + j];
+            q.w = 0.f;
+            P[j] = q;
+        }
+        qx[u] = q.x;
+        qy[u] = q.y;
+        qz[u] = q.z;
+    }
+    __syncwarp();
+
+    double E = S.E[g];
+    const int slot = S.temp_of_rep[g];
+    const int gs = rd.slot_base + slot;
+    const float Tf = S.Tf[gs];
+    const uint32_t k0 = (uint32_t)ed.seed, k1 = (uint32_t)(ed.seed >> 32);
+    const uint32_t c3 = ed.ens_id | (kTagMove << 24);
+    const bool ljb = ed.lj_bonded != 0;
+    const float delta = ed.delta;
+    const float kInf = __int_as_float(0x7f800000);
+    const float sum_err = (float)(U + 3) * kEps0;
+
+    for (; s < s_end; ++s) {
+        const bool logging = S.log_bead && s >= S.log_s0 && s < S.log_s0 + S.log_ns;
+        const size_t lrow = logging ? (size_t)(s - S.log_s0) * S.log_pstride + rd.pos_off : 0;
+        df dsum = {0.f, 0.f};
+        int nacc = 0;
+        for (int m0 = 0; m0 < N; m0 += 32) {
+            // ---- batch: draws of move m0 + lane, its bonds at batch start, conflicts
+            const int mc = min(32, N - m0);
+            int km = 0;
+            if (lane < mc) {
+                const uint32_t m = (uint32_t)(m0 + lane);
+                const u4 w = philox(u4{2u * m, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                const u4 v = philox(u4{2u * m + 1u, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                km = (int)__umulhi(w.x, (uint32_t)N);
+                const float sx = __fsub_rn(__fmul_rn(2.f, unif24(w.y)), 1.f);
+                const float sy = __fsub_rn(__fmul_rn(2.f, unif24(w.z)), 1.f);
+                const float sz = __fsub_rn(__fmul_rn(2.f, unif24(w.w)), 1.f);
+                const float th = __fmul_rn(-logf(unif24(v.x)), Tf);
+                const float4 q = P[km];
+                const float3 pk = make_float3(q.x, q.y, q.z);
+                const float3 pnk = make_float3(__fadd_rn(q.x, __fmul_rn(delta, sx)), __fadd_rn(q.y, __fmul_rn(delta, sy)),
+                                               __fadd_rn(q.z, __fmul_rn(delta, sz)));
+                float bt = 0.f, be = 0.f;
+                unsigned bfl = 0u;  // bit 0: inexact, bit 1: edge
+                if (km > 0) {
+                    const BondF a = bond_f32(P[km - 1], pk, pnk, ljb);
+                    bt = a.t;
+                    be = a.e;
+                    bfl |= (a.inexact ? 1u : 0u) | (a.edge ? 2u : 0u);
+                }
+                if (km + 1 < N) {
+                    const BondF c = bond_f32(P[km + 1], pk, pnk, ljb);
+                    bt = __fadd_rn(bt, c.t);
+                    be = __fadd_rn(be, c.e);
+                    bfl |= (c.inexact ? 1u : 0u) | (c.edge ? 2u : 0u);
+                }
+                D0[lane] = make_float4(__int_as_float(km | (int)(bfl << 16)), sx, sy, sz);
+                D1[lane] = make_float4(th, bt, be, 0.f);
+            }
+            unsigned cm = 0u;  // earlier moves of the batch on bead km or a bonded neighbour
+#pragma unroll 8
+            for (int l = 0; l < 31; ++l) {
+                const int kl = __shfl_sync(kFull, km, l);
+                if (l < lane && abs(kl - km) <= 1) cm |= 1u << l;
+            }
+            if (lane < mc) D1[lane].w = __uint_as_float(cm);
+            __syncwarp();
+            unsigned amask = 0u;  // accepted moves of the batch
+            // the next move's draws and bead, fetched while the current move is evaluated
+            float4 d0N = D0[0], d1N = D1[0];
+            float4 pN = P[__float_as_int(d0N.x) & 0xffff];
+            for (int b = 0; b < mc; ++b) {
+                const int kw = __float_as_int(d0N.x), k = kw & 0xffff;
+                const unsigned bfb = (unsigned)kw >> 16, cmb = __float_as_uint(d1N.w);
+                const float theta = d1N.x, btb = d1N.y, beb = d1N.z;
+                const float3 p = make_float3(pN.x, pN.y, pN.z);
+                const float3 pn = make_float3(__fadd_rn(p.x, __fmul_rn(delta, d0N.y)), __fadd_rn(p.y, __fmul_rn(delta, d0N.z)),
+                                              __fadd_rn(p.z, __fmul_rn(delta, d0N.w)));
+                int kN = -1;
+                if (b + 1 < mc) {
+                    d0N = D0[b + 1];
+                    d1N = D1[b + 1];
+                    kN = __float_as_int(d0N.x) & 0xffff;
+                    pN = P[kN];  // forwarded below if this move stores bead kN
+                }
+                // ---- FP32 row over the non-bonded partners, with its error weights
+                const RowSums rs = row_pass<U>(qx, qy, qz, p, pn, k, lane, N);
+                // ---- bonds: the batch value unless an accepted earlier move made it stale
+                float bnd = 0.f, bnde = 0.f;
+                unsigned bf = 0u;
+                if ((cmb & amask) == 0u) {
+                    if (lane == 0) {
+                        bnd = btb;
+                        bnde = beb;
+                        bf = bfb;
+                    }
+                } else if (lane < 2) {
+                    const int j = lane == 0 ? k - 1 : k + 1;
+                    if (j >= 0 && j < N) {
+                        const BondF x = bond_f32(P[j], p, pn, ljb);
+                        bnd = x.t;
+                        bnde = x.e;
+                        bf = (x.inexact ? 1u : 0u) | (x.edge ? 2u : 0u);
+                    }
+                }
+                // ---- exact fixed-point warp sums of lower and upper bounds of the shares
+                const float part = __fadd_rn(__fadd_rn(rs.aord, rs.ast), bnd);
+                // a broken bond (+inf) leaves the lower bound at +inf: a certain rejection
+                const float bab = fabsf(bnd) < kInf ? fabsf(bnd) : 0.f;
+                const float el = __fmaf_rn(kDeltaX, rs.sw, __fmaf_rn(sum_err, __fadd_rn(rs.sab, bab), bnde));
+                const float lb = __fsub_rd(part, el), ub = __fadd_ru(part, el);
+                // a bound is clamped only in the direction that keeps it a bound; a share
+                // beyond the other side (or NaN, or a bond at the FENE wall) voids that sum
+                const bool lo_bad = !(lb >= -kQMax) || (bf & 2u);
+                const bool hi_bad = !(ub <= kQMax) || (bf & 2u);
+                const int ql = lo_bad ? 0 : __float2int_rd(__fmul_rd(fminf(lb, kQMax), kQ));
+                const int qh = hi_bad ? 0 : __float2int_ru(__fmul_ru(fmaxf(ub, -kQMax), kQ));
+                const int sl = __reduce_add_sync(kFull, ql);
+                const int sh = __reduce_add_sync(kFull, qh);
+                const unsigned fl = __reduce_or_sync(kFull, (lo_bad ? 1u : 0u) | (hi_bad ? 2u : 0u) |
+                                                                (rs.stm ? 4u : 0u) | ((bf & 3u) ? 8u : 0u));
+                // ---- decision (Eq. 5): certain unless theta lies inside [lower, upper]
+                bool accept = false, sure = false;
+                if (!(fl & 1u) && __fmul_rd(__int2float_rd(sl), kQInv) >= theta) {
+                    sure = true;
+                } else if (!(fl & 2u) && __fmul_ru(__int2float_ru(sh), kQInv) < theta) {
+                    sure = true;
+                    accept = true;
+                }
+                float dE = 0.f;
+                if (accept || !sure || logging) {
+                    if (fl & 12u) {
+                        // the accurate value: steep pairs and inexact bonds in double-float
+                        float a2 = rs.aord;
+                        if (fl & 4u) {
+                            const int cnt = __popc(rs.stm);
+                            int pre = cnt;  // inclusive prefix of the steep counts over the lanes
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int y = __shfl_up_sync(kFull, pre, o);
+                                if (lane >= o) pre += y;
+                            }
+                            const int qn = __shfl_sync(kFull, pre, 31);
+                            int at = pre - cnt;
+                            for (unsigned m = rs.stm; m; m &= m - 1) Q[at++] = lane + 32 * (__ffs(m) - 1);
+                            __syncwarp();
+                            a2 = __fadd_rn(a2, steep_pairs(Q, qn, P, p, pn, -1, pN, lane));
+                        }
+                        float bacc = bnd;
+                        if (fl & 8u) {
+                            bacc = 0.f;
+                            if (lane < 2) {
+                                const int j = lane == 0 ? k - 1 : k + 1;
+                                if (j >= 0 && j < N) {
+                                    bool brk = false;
+                                    bacc = bond_term_team(P[j], p, pn, ljb, &brk);
+                                    if (brk) bacc = kInf;
+                                }
+                            }
+                        }
+                        dE = warp_sum(__fadd_rn(a2, bacc));
+                        __syncwarp();  // the queue is read before the next move writes it
+                    } else {
+                        dE = warp_sum(part);
+                    }
+                    if (!sure) accept = dE < theta;  // NaN and +inf reject
+                }
+                if (accept) {
+                    if (lane == (k & 31)) {
+                        const int su = k >> 5;
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            if (u == su) {
+                                qx[u] = pn.x;
+                                qy[u] = pn.y;
+                                qz[u] = pn.z;
+                            }
+                    }
+                    if (lane == 0) P[k] = make_float4(pn.x, pn.y, pn.z, 0.f);
+                    if (kN == k) pN = make_float4(pn.x, pn.y, pn.z, 0.f);
+                    amask |= 1u << b;
+                    dsum = df_add(dsum, df{dE, 0.f});
+                    ++nacc;
+                }
+                if (logging && lane == 0) {
+                    const size_t li = lrow + m0 + b;
+                    S.log_bead[li] = k;
+                    S.log_de[li] = dE;
+                    S.log_theta[li] = theta;
+                    S.log_acc[li] = accept ? 1 : 0;
+                }
+                __syncwarp();
+            }
+        }
+        E = (E + (double)dsum.hi) + (double)dsum.lo;
+        sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
+    }
+    __syncwarp();
+    for (int j = lane; j < N; j += 32) S.pos[rd.pos_off + j] = P[j];
+    if (lane == 0) {
+        S.E[g] = E;
+        S.rep_sweep[g] = s_end;
+    }
+}
+
+int reg_slots(int nmax) {
+    int u = 1;
+    while (32 * u < nmax) u <<= 1;
+    return u;
+}
+
+size_t reg_smem_bytes(int nmax) { return (size_t)nmax * (sizeof(float4) + sizeof(int)) + 64 * sizeof(float4); }
+
+cudaError_t launch_sweep_reg(const State& s, int chunk, cudaStream_t st) {
+    const size_t smem = reg_smem_bytes(s.nmax);
+    switch (reg_slots(s.nmax)) {
+        case 1: k_sweep_reg<1><<<s.n_reps, 32, smem, st>>>(s, chunk); break;
+        case 2: k_sweep_reg<2><<<s.n_reps, 32, smem, st>>>(s, chunk); break;
+        case 4: k_sweep_reg<4><<<s.n_reps, 32, smem, st>>>(s, chunk); break;
+        case 8: k_sweep_reg<8><<<s.n_reps, 32, smem, st>>>(s, chunk); break;
+        case 16: k_sweep_reg<16><<<s.n_reps, 32, smem, st>>>(s, chunk); break;
+        case 32: k_sweep_reg<32><<<s.n_reps, 32, smem, st>>>(s, chunk); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ptgb

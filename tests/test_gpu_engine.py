@@ -208,7 +208,7 @@ def test_autotune_leaves_the_state_untouched():
         before = _state(h)
         c0 = pt.pt_counters(h)
         v = pt.pt_autotune(h, 4, force=True)
-        assert v in (0, 1, 2, 3) and pt.pt_get_sweep_kernel(h) == v
+        assert v in (0, 1, 2, 3, 4) and pt.pt_get_sweep_kernel(h) == v
         _same(_state(h), before)
         assert pt.pt_counters(h) == c0
         assert pt.pt_autotune(h, 4) == v  # cached
@@ -218,7 +218,7 @@ def test_autotune_leaves_the_state_untouched():
         pt.pt_destroy(h)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_every_kernel_keeps_the_batch_bit_identical_to_separate_runs(variant):
     """Per-ensemble results do not depend on which ensembles share the launch."""
     specs = [(20, 4, 1, 0), (45, 7, 2, 1)]
@@ -242,3 +242,29 @@ def test_every_kernel_keeps_the_batch_bit_identical_to_separate_runs(variant):
         finally:
             pt.pt_destroy(h)
         po += 3 * R * N
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_the_move_log_does_not_change_the_chain(variant):
+    """With the per-move log on, kernels may evaluate more terms accurately (kernel 4 refines
+    every move with a steep pair); the chain itself must be the same bit for bit."""
+    T = inputs.temperature_ladder(0.2, 3.0, 12)
+    x0 = inputs.random_coil(70, 12, 31)
+    out = []
+    for log in (False, True):
+        p, keep = pt.make_params(70, T, 31, init_positions=x0, n_bins=128, recompute_every=0)
+        h = pt.pt_create_ex(p)
+        try:
+            pt.pt_set_sweep_kernel(h, variant)
+            if log:
+                pt.pt_set_debug_log(h, 0, 40)
+            pt.pt_sweep(h, 40, 1)
+            out.append(dict(pos=pt.pt_get_positions(h), rot=pt.pt_get_permutation(h), E=pt.pt_energies(h),
+                            hist=pt.pt_histograms(h), acc=pt.pt_acceptance(h)))
+        finally:
+            pt.pt_destroy(h)
+    a, b = out
+    assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["rot"], b["rot"])
+    assert np.array_equal(a["E"], b["E"]) and np.array_equal(a["hist"], b["hist"])
+    for x, y in zip(a["acc"], b["acc"]):
+        assert np.array_equal(x, y)

@@ -133,6 +133,20 @@ int pt_get_permutation(pt_ctx* h, int32_t* rep_of_temp, int n);
 /* Per temperature slot: count, sum E, sum E^2 (FP64), the inputs of Eq. 7; n == 3 x slots. */
 int pt_moments(pt_ctx* h, double* out, int64_t n);
 
+/* Shape observables (Sec. 4.1), per temperature slot, measured with the energy after every
+ * sweep from n_therm on: sum of r_gyr^2 (Eq. 8: mean squared distance of the beads from
+ * their centre of mass), of r_gyr^4, of R_ee^2 (squared end-to-end distance), of R_ee^4, of
+ * E r_gyr^2 and of E R_ee^2; [slot][6] FP64, n == 6 x slots. With the measurement count of
+ * pt_moments these give <r_gyr^2>, its variance, and the fluctuation
+ * d<r_gyr^2>/dT = beta^2 (<E r_gyr^2> - <E><r_gyr^2>). Computed in FP64 from the float
+ * coordinates, so they equal an FP64 evaluation up to summation order. */
+int pt_observables(pt_ctx* h, double* out, int64_t n);
+
+/* Per temperature slot and energy bin (the layout of pt_histograms): the sums of r_gyr^2 and
+ * of R_ee^2 over the measurements counted in that bin, for reweighting; n == slots x n_bins
+ * for each array; either pointer may be NULL. */
+int pt_obs_histograms(pt_ctx* h, double* rg2, double* ree2, int64_t n);
+
 /* Per temperature slot: measurements below e_min and at or above e_max; n == 2 x slots. */
 int pt_hist_outliers(pt_ctx* h, double* out, int64_t n);
 

@@ -188,9 +188,9 @@ cudaError_t dalloc(T** p, size_t n) {
 void free_state(pt_ctx* h) {
     State& S = h->S;
     void* ptrs[] = {S.reps, S.ens, S.pos, S.E, S.temp_of_rep, S.rep_of_temp, S.Tf, S.beta, S.hist,
-                    S.outl, S.mom, S.mv_att, S.mv_acc, S.ex_att, S.ex_acc, S.drift, S.rep_sweep, S.err,
-                    S.log_bead, S.log_de, S.log_theta, S.log_acc, S.log_e, S.log_x,
-                    h->scratch, h->conf_buf, h->eout_buf};
+                    S.outl, S.mom, S.obs, S.obs_rg2_hist, S.obs_ree2_hist, S.mv_att, S.mv_acc, S.ex_att,
+                    S.ex_acc, S.drift, S.rep_sweep, S.err, S.log_bead, S.log_de, S.log_theta, S.log_acc,
+                    S.log_e, S.log_x, h->scratch, h->conf_buf, h->eout_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     S = State{};
@@ -347,6 +347,9 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     A(dalloc(&S.hist, (size_t)h->H));
     A(dalloc(&S.outl, 2 * G));
     A(dalloc(&S.mom, 3 * G));
+    A(dalloc(&S.obs, 6 * G));
+    A(dalloc(&S.obs_rg2_hist, (size_t)h->H));
+    A(dalloc(&S.obs_ree2_hist, (size_t)h->H));
     A(dalloc(&S.mv_att, G));
     A(dalloc(&S.mv_acc, G));
     A(dalloc(&S.ex_att, G));
@@ -814,6 +817,22 @@ extern "C" int pt_moments(pt_ctx* h, double* out, int64_t n) {
     return copy_out(h, out, h->S.mom, 3 * (size_t)h->G);
 }
 
+extern "C" int pt_observables(pt_ctx* h, double* out, int64_t n) {
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (!out || n != 6 * (int64_t)h->G) return fail(PT_EINVAL, "pt_observables: n=%lld, need %d", (long long)n, 6 * h->G);
+    return copy_out(h, out, h->S.obs, 6 * (size_t)h->G);
+}
+
+extern "C" int pt_obs_histograms(pt_ctx* h, double* rg2, double* ree2, int64_t n) {
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (n != (int64_t)h->H) return fail(PT_EINVAL, "pt_obs_histograms: n=%lld, need %lld", (long long)n, (long long)h->H);
+    if (rg2 && (rc = copy_out(h, rg2, h->S.obs_rg2_hist, (size_t)h->H))) return rc;
+    if (ree2 && (rc = copy_out(h, ree2, h->S.obs_ree2_hist, (size_t)h->H))) return rc;
+    return PT_OK;
+}
+
 extern "C" int pt_hist_outliers(pt_ctx* h, double* out, int64_t n) {
     int rc = check_usable(h);
     if (rc) return rc;
@@ -952,6 +971,9 @@ std::vector<Blob> blobs(pt_ctx* h) {
             {"hist", S.hist, (size_t)h->H * sizeof(double)},
             {"outl", S.outl, 2 * G * sizeof(double)},
             {"mom", S.mom, 3 * G * sizeof(double)},
+            {"obs", S.obs, 6 * G * sizeof(double)},
+            {"obs_rg2", S.obs_rg2_hist, (size_t)h->H * sizeof(double)},
+            {"obs_ree2", S.obs_ree2_hist, (size_t)h->H * sizeof(double)},
             {"mv_att", S.mv_att, G * 8},
             {"mv_acc", S.mv_acc, G * 8},
             {"ex_att", S.ex_att, G * 8},

@@ -48,6 +48,9 @@ struct State {
     double* outl;             // [slot][2]
     double* mom;              // [slot][3]
     unsigned long long *mv_att, *mv_acc, *ex_att, *ex_acc;  // [slot]
+    double* obs;              // [slot][6] sum rg2, rg2^2, ree2, ree2^2, E rg2, E ree2 (null: off)
+    double* obs_rg2_hist;     // [sum R n_bins] sum of rg2 per energy bin (layout of hist)
+    double* obs_ree2_hist;    // [sum R n_bins] sum of ree2 per energy bin
     double* drift;            // [replica]
     int64_t* rep_sweep;       // [replica] sweeps done
     int* err;                 // error bits

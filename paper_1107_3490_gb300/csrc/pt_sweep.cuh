@@ -42,6 +42,32 @@ static __device__ double warp_full_energy(const float4* P, int N, int lj_bonded,
 }
 
 
+// Shape observables of the chain in shared memory (Sec. 4.1), in FP64 by one warp: the
+// squared radius of gyration (Eq. 8; centre of mass first, then the mean squared distance
+// from it) and the squared end-to-end distance. Results in every lane.
+__device__ __forceinline__ void warp_shape(const float4* P, int N, int lane, double& rg2, double& ree2) {
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+    for (int i = lane; i < N; i += 32) {
+        const float4 q = P[i];
+        cx += q.x;
+        cy += q.y;
+        cz += q.z;
+    }
+    cx = warp_sum_d(cx) / N;
+    cy = warp_sum_d(cy) / N;
+    cz = warp_sum_d(cz) / N;
+    double g = 0.0;
+    for (int i = lane; i < N; i += 32) {
+        const float4 q = P[i];
+        const double dx = q.x - cx, dy = q.y - cy, dz = q.z - cz;
+        g += dx * dx + dy * dy + dz * dz;
+    }
+    rg2 = warp_sum_d(g) / N;
+    const float4 a = P[0], b = P[N - 1];
+    const double ex = (double)b.x - a.x, ey = (double)b.y - a.y, ez = (double)b.z - a.z;
+    ree2 = ex * ex + ey * ey + ez * ez;
+}
+
 // End of one sweep of replica g (all lanes of its warp call it): the periodic FP64
 // recompute of Eq. 4, then the measurement into the replica's temperature slot (the
 // replica owns the slot until the next exchange, so plain read-modify-write is race-free)
@@ -54,23 +80,44 @@ __device__ __forceinline__ void sweep_epilogue(const State& S, const EnsDev& ed,
         if (lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
         E = full;
     }
+    const bool measure = isfinite(E) && s >= ed.n_therm;
+    double rg2 = 0.0, ree2 = 0.0;
+    if (measure && S.obs) warp_shape(P, N, lane, rg2, ree2);
     if (lane == 0) {
         // Fire-and-forget atomic adds (no value returned, so the warp does not wait on L2).
         // The slot has a single writer until the next exchange and one thread's adds to an
         // address apply in program order, so the sums are deterministic.
         if (!isfinite(E)) {
             atomicOr(S.err, kErrNonFinite);
-        } else if (s >= ed.n_therm) {
+        } else if (measure) {
+            int64_t hi = -1;  // histogram index of this measurement
             if (E < ed.e_min) {
                 atomicAdd(&S.outl[2 * gs], 1.0);
             } else {
                 const double b = floor((E - ed.e_min) * ed.inv_w);
-                if (b >= (double)ed.n_bins) atomicAdd(&S.outl[2 * gs + 1], 1.0);
-                else atomicAdd(&S.hist[ed.hist_base + (int64_t)slot * ed.n_bins + (int64_t)b], 1.0);
+                if (b >= (double)ed.n_bins) {
+                    atomicAdd(&S.outl[2 * gs + 1], 1.0);
+                } else {
+                    hi = ed.hist_base + (int64_t)slot * ed.n_bins + (int64_t)b;
+                    atomicAdd(&S.hist[hi], 1.0);
+                }
             }
             atomicAdd(&S.mom[3 * gs], 1.0);
             atomicAdd(&S.mom[3 * gs + 1], E);
             atomicAdd(&S.mom[3 * gs + 2], E * E);
+            if (S.obs) {
+                double* o = S.obs + 6 * (int64_t)gs;
+                atomicAdd(o, rg2);
+                atomicAdd(o + 1, rg2 * rg2);
+                atomicAdd(o + 2, ree2);
+                atomicAdd(o + 3, ree2 * ree2);
+                atomicAdd(o + 4, E * rg2);
+                atomicAdd(o + 5, E * ree2);
+                if (hi >= 0) {
+                    atomicAdd(&S.obs_rg2_hist[hi], rg2);
+                    atomicAdd(&S.obs_ree2_hist[hi], ree2);
+                }
+            }
         }
         atomicAdd(&S.mv_att[gs], (unsigned long long)N);
         atomicAdd(&S.mv_acc[gs], (unsigned long long)nacc);

@@ -67,6 +67,8 @@ _SIGS = {
     "pt_set_positions": (_I, [_V, _V, _I64]),
     "pt_get_permutation": (_I, [_V, _V, _I]),
     "pt_moments": (_I, [_V, _V, _I64]),
+    "pt_observables": (_I, [_V, _V, _I64]),
+    "pt_obs_histograms": (_I, [_V, _V, _V, _I64]),
     "pt_hist_outliers": (_I, [_V, _V, _I64]),
     "pt_acceptance": (_I, [_V, _V, _V, _V, _V, _I]),
     "pt_drift": (_I, [_V, _V, _I]),
@@ -243,6 +245,21 @@ def pt_moments(h) -> np.ndarray:
     out = np.zeros(3 * pt_total_replicas(h), dtype=np.float64)
     _ck(lib().pt_moments(h, _p(out), out.size))
     return out.reshape(-1, 3)
+
+
+def pt_observables(h) -> np.ndarray:
+    """[slots, 6]: sums of rg2, rg2^2, ree2, ree2^2, E rg2, E ree2 per temperature slot."""
+    out = np.zeros(6 * pt_total_replicas(h), dtype=np.float64)
+    _ck(lib().pt_observables(h, _p(out), out.size))
+    return out.reshape(-1, 6)
+
+
+def pt_obs_histograms(h, n: int):
+    """Per-bin sums of rg2 and ree2 (layout of pt_histograms, n entries each)."""
+    rg2 = np.zeros(n, dtype=np.float64)
+    ree2 = np.zeros(n, dtype=np.float64)
+    _ck(lib().pt_obs_histograms(h, _p(rg2), _p(ree2), n))
+    return rg2, ree2
 
 
 def pt_hist_outliers(h) -> np.ndarray:

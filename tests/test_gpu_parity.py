@@ -41,7 +41,8 @@ def _run(N, R, S, seed, xe=1, delta=0.3, lj_bonded=1, tmin=0.3, tmax=3.0, recomp
         out = dict(E=pt.pt_energies(h), pos=pt.pt_get_positions(h).reshape(R, N, 3),
                    rot=pt.pt_get_permutation(h), hist=pt.pt_histograms(h).reshape(R, n_bins),
                    mom=pt.pt_moments(h), outl=pt.pt_hist_outliers(h), acc=pt.pt_acceptance(h),
-                   drift=pt.pt_drift(h), counters=pt.pt_counters(h, 0))
+                   drift=pt.pt_drift(h), counters=pt.pt_counters(h, 0), obs=pt.pt_observables(h),
+                   obs_hist=pt.pt_obs_histograms(h, R * n_bins))
     finally:
         pt.pt_destroy(h)
     orc = oracle.OracleEnsemble(x0, T, seed, ensemble_id=ens_id, delta=delta, lj_bonded=lj_bonded,
@@ -70,6 +71,17 @@ def _full_match(rep, out, orc, S):
     assert np.abs(out["hist"] - orc.hist).sum() <= 2
     np.testing.assert_allclose(out["mom"][:, 0], orc.mom[:, 0], rtol=0, atol=0)
     np.testing.assert_allclose(out["mom"][:, 1], orc.mom[:, 1], rtol=1e-9, atol=S * rep.max_e_err + 1e-9)
+    # shape observables (Sec. 4.1): FP64 on both sides from the same float coordinates, so
+    # they agree up to summation order; the E-weighted sums carry the energy tolerance
+    np.testing.assert_allclose(out["obs"][:, :4], orc.obs[:, :4], rtol=1e-12, atol=0)
+    scale = np.max(np.abs(orc.obs[:, [0, 2]]), axis=1) + 1e-30
+    for c in (4, 5):
+        np.testing.assert_allclose(out["obs"][:, c], orc.obs[:, c], rtol=1e-9,
+                                   atol=float(np.max(scale)) * (rep.max_e_err + 1e-12) * 2)
+    g_rg, g_re = (x.reshape(R, -1) for x in out["obs_hist"])
+    same = out["hist"] == orc.hist
+    np.testing.assert_allclose(g_rg[same], orc.obs_rg2_hist[same], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(g_re[same], orc.obs_ree2_hist[same], rtol=1e-12, atol=0)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])

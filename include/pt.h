@@ -147,6 +147,28 @@ int pt_observables(pt_ctx* h, double* out, int64_t n);
  * for each array; either pointer may be NULL. */
 int pt_obs_histograms(pt_ctx* h, double* rg2, double* ree2, int64_t n);
 
+/* Multiple-histogram reweighting (Ferrenberg and Swendsen 1989) of one ensemble's per-slot
+ * energy histograms (pt_histograms rows, [n_temps][n_bins] FP64, host memory) into the log
+ * density of states. The paper gives C_V/N = beta^2/N (<E^2> - <E>^2) at the simulated
+ * temperatures (Sec. 4.1, Eq. 7); the density of states gives it at any temperature. It
+ * iterates g(E_b) = sum_k H_k(b) / sum_k n_k exp(f_k - E_b / T_k) and
+ * exp(-f_k) = sum_b g(E_b) exp(-E_b / T_k) in FP64 log space until max |delta f| < tol (or
+ * max_iter), with f = 0 at the first slot that has samples; bin b stands for its centre
+ * E_b = e_min + (b + 1/2)(e_max - e_min)/n_bins. Out: ln_g[n_bins] (-inf for empty bins),
+ * f[n_temps] (NaN for slots without samples; may be NULL), *iterations (may be NULL).
+ * Host code: needs no GPU. PT_EINVAL on a bad size, a non-positive temperature or a
+ * negative or non-finite count. */
+int pt_wham(int n_temps, int n_bins, const double* temperatures, const double* hist, double e_min,
+            double e_max, double tol, int max_iter, double* ln_g, double* f, int* iterations);
+
+/* Canonical averages from ln_g (pt_wham) at n_out temperatures: out[i][4] = <E>,
+ * C_V = (<E^2> - <E>^2) / T^2, and, when obs_sum and counts are given (per-bin sums of an
+ * observable over all slots, e.g. pt_obs_histograms summed over slots, and the per-bin
+ * counts summed over slots), <O> and d<O>/dT = (<E O> - <E><O>) / T^2 from the
+ * microcanonical means O(E_b) = obs_sum[b] / counts[b]; NaN otherwise. Host code. */
+int pt_wham_canonical(int n_bins, double e_min, double e_max, const double* ln_g, const double* obs_sum,
+                      const double* counts, int n_out, const double* temperatures, double* out);
+
 /* Per temperature slot: measurements below e_min and at or above e_max; n == 2 x slots. */
 int pt_hist_outliers(pt_ctx* h, double* out, int64_t n);
 

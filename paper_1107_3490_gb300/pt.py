@@ -68,6 +68,8 @@ _SIGS = {
     "pt_get_permutation": (_I, [_V, _V, _I]),
     "pt_moments": (_I, [_V, _V, _I64]),
     "pt_observables": (_I, [_V, _V, _I64]),
+    "pt_wham": (_I, [_I, _I, _V, _V, _D, _D, _D, _I, _V, _V, _V]),
+    "pt_wham_canonical": (_I, [_I, _D, _D, _V, _V, _V, _I, _V, _V]),
     "pt_obs_histograms": (_I, [_V, _V, _V, _I64]),
     "pt_hist_outliers": (_I, [_V, _V, _I64]),
     "pt_acceptance": (_I, [_V, _V, _V, _V, _V, _I]),
@@ -260,6 +262,34 @@ def pt_obs_histograms(h, n: int):
     ree2 = np.zeros(n, dtype=np.float64)
     _ck(lib().pt_obs_histograms(h, _p(rg2), _p(ree2), n))
     return rg2, ree2
+
+
+def pt_wham(temperatures, hist, e_min: float, e_max: float, tol: float = 1e-12, max_iter: int = 200000):
+    """Multiple-histogram reweighting: (ln_g [n_bins], f [K], iterations). Host code."""
+    T = np.ascontiguousarray(temperatures, dtype=np.float64)
+    H = np.ascontiguousarray(hist, dtype=np.float64)
+    if H.ndim != 2 or H.shape[0] != T.size:
+        raise ValueError("hist must be [n_temps, n_bins]")
+    ln_g = np.zeros(H.shape[1], dtype=np.float64)
+    f = np.zeros(T.size, dtype=np.float64)
+    it = ctypes.c_int(0)
+    _ck(lib().pt_wham(T.size, H.shape[1], _p(T), _p(H), float(e_min), float(e_max), float(tol), int(max_iter),
+                      _p(ln_g), _p(f), ctypes.byref(it)))
+    return ln_g, f, it.value
+
+
+def pt_wham_canonical(ln_g, e_min: float, e_max: float, temperatures, obs_sum=None, counts=None) -> np.ndarray:
+    """[n_T, 4]: <E>, C_V, <O>, d<O>/dT at each temperature (host code)."""
+    g = np.ascontiguousarray(ln_g, dtype=np.float64)
+    T = np.ascontiguousarray(temperatures, dtype=np.float64)
+    out = np.zeros((T.size, 4), dtype=np.float64)
+    o = c = None
+    if obs_sum is not None:
+        o = np.ascontiguousarray(obs_sum, dtype=np.float64)
+        c = np.ascontiguousarray(counts, dtype=np.float64)
+    _ck(lib().pt_wham_canonical(g.size, float(e_min), float(e_max), _p(g), _p(o) if o is not None else None,
+                                _p(c) if c is not None else None, T.size, _p(T), _p(out)))
+    return out
 
 
 def pt_hist_outliers(h) -> np.ndarray:

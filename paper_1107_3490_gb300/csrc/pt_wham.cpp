@@ -8,10 +8,11 @@
 //     exp(-f_k) = sum_b g(E_b) exp(-beta_k E_b),
 // iterated to self-consistency with f fixed to 0 at the first slot that has samples. All
 // sums are log-sum-exp in FP64; a bin is its centre E_b = e_min + (b + 1/2) w; bins with no
-// counts have g = 0. The bins are split over host threads; every thread owns a fixed range
-// of bins and the per-slot sums are combined in thread order, so results do not depend on
-// scheduling.
+// counts have g = 0. A fixed team of host threads runs the iteration; every thread owns a
+// fixed range of bins and the per-slot sums are combined in thread order, so results do not
+// depend on scheduling.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -83,6 +84,28 @@ void parallel_ranges(int nt, int n, F&& f) {
     for (auto& x : th) x.join();
 }
 
+// Reusable barrier for the fixed team of the fixed-point iteration: spins briefly, then
+// yields (the iteration's phases are tens of microseconds long).
+class SpinBarrier {
+  public:
+    explicit SpinBarrier(int n) : n_(n) {}
+    void wait() {
+        const unsigned gen = gen_.load(std::memory_order_acquire);
+        if (count_.fetch_add(1, std::memory_order_acq_rel) + 1 == n_) {
+            count_.store(0, std::memory_order_relaxed);
+            gen_.fetch_add(1, std::memory_order_acq_rel);
+            return;
+        }
+        for (int spin = 0; gen_.load(std::memory_order_acquire) == gen; ++spin)
+            if (spin > 2000) std::this_thread::yield();
+    }
+
+  private:
+    const int n_;
+    std::atomic<int> count_{0};
+    std::atomic<unsigned> gen_{0};
+};
+
 }  // namespace
 
 extern "C" int pt_wham(int n_temps, int n_bins, const double* temperatures, const double* hist, double e_min,
@@ -139,29 +162,49 @@ extern "C" int pt_wham(int n_temps, int n_bins, const double* temperatures, cons
             lg[i] = ln_tot[i] - d.value();
         }
     };
+    // The team of nt threads runs every iteration: each thread its own bin range (ln g, then
+    // per-slot partial sums), a barrier, thread 0 combines in thread order and tests
+    // convergence, a barrier, all threads read the verdict.
     int it = 0;
-    for (it = 1; it <= max_iter; ++it) {
-        parallel_ranges(nt, B, [&](int t, int a, int b) {
+    bool done = false;
+    SpinBarrier bar(nt);
+    auto team = [&](int t) {
+        const int a = (int)((int64_t)B * t / nt), b = (int)((int64_t)B * (t + 1) / nt);
+        for (int i = 1; i <= max_iter; ++i) {
             density(t, a, b);
             for (int k = 0; k < K; ++k) {
                 Lse z;
-                for (int i = a; i < b; ++i) z.add(lg[i] - beta[k] * E[i]);
+                for (int j = a; j < b; ++j) z.add(lg[j] - beta[k] * E[j]);
                 part[t][k] = z;
             }
-        });
-        for (int k = 0; k < K; ++k) {
-            Lse z;
-            for (int t = 0; t < nt; ++t) z.merge(part[t][k]);
-            fnew[k] = -z.value();
+            bar.wait();
+            if (t == 0) {
+                for (int k = 0; k < K; ++k) {
+                    Lse z;
+                    for (int u = 0; u < nt; ++u) z.merge(part[u][k]);
+                    fnew[k] = -z.value();
+                }
+                const double f0 = fnew[0];
+                double diff = 0.0;
+                for (int k = 0; k < K; ++k) {
+                    fnew[k] -= f0;
+                    diff = std::max(diff, std::fabs(fnew[k] - fk[k]));
+                }
+                fk.swap(fnew);
+                it = i;
+                done = diff < tol || i == max_iter;
+            }
+            bar.wait();
+            if (done) break;
         }
-        const double f0 = fnew[0];
-        double diff = 0.0;
-        for (int k = 0; k < K; ++k) {
-            fnew[k] -= f0;
-            diff = std::max(diff, std::fabs(fnew[k] - fk[k]));
-        }
-        fk.swap(fnew);
-        if (diff < tol) break;
+    };
+    if (nt <= 1) {
+        team(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 1; t < nt; ++t) th.emplace_back(team, t);
+        team(0);
+        for (auto& x : th) x.join();
     }
     if (it > max_iter) it = max_iter;
     parallel_ranges(nt, B, density);

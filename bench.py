@@ -30,7 +30,8 @@ N_BEADS, N_REP, N_ENS, T_MIN, T_MAX = 100, 64, 4, 0.2, 3.0
 SWEEPS_PER_STEP = 1000
 FLOPS_PER_PAIR = 15  # FP32 flops per pair evaluation (FMA = 2), see the design notes
 METRIC = "single-bead Metropolis updates/sec (all replicas)"
-KERNEL_NAMES = {0: "k_sweep", 1: "k_sweep_la", 2: "k_sweep_team", 3: "k_sweep_wpm", 4: "k_sweep_reg"}
+KERNEL_NAMES = {0: "k_sweep", 1: "k_sweep_la", 2: "k_sweep_team", 3: "k_sweep_wpm", 4: "k_sweep_reg",
+                5: "k_sweep_grp"}
 UNIT = "updates/s"
 WORKLOAD = (f"PT polymer N={N_BEADS} beads, {N_REP} replicas at T geometric {T_MIN}-{T_MAX}, "
             f"{N_ENS} ensembles (seeds 1-{N_ENS}) per GPU, delta 0.3, exchange every sweep, "
@@ -276,7 +277,8 @@ def run_gpu(args):
                        "l2": "256 MB buffer written between timed steps (outside the per-step events)",
                        "sweep_kernel": {0: "warp per replica", 1: "lookahead groups of 8 moves",
                                         2: "team of warps per replica", 3: "warp per move of a group",
-                                        4: "warp per replica, chain in registers, deferred double-float"}[kernel],
+                                        4: "warp per replica, chain in registers, deferred double-float",
+                                        5: "CTA per replica, one warp per move of a group, chain in registers"}[kernel],
                        "pair_evals_per_s": value * 2 * (N_BEADS - 1)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "clocks": clocks}
@@ -518,9 +520,9 @@ def main(argv=None):
     ap.add_argument("--jobs", type=int, default=200)
     ap.add_argument("--rate", type=float, default=40.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4],
+    ap.add_argument("--kernel", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5],
                     help="sweep kernel: -1 autotune (default), 0 warp per replica, 1 lookahead groups, "
-                         "2 team of warps, 3 warp per move of a group, 4 chain in registers")
+                         "2 team of warps, 3 warp per move of a group, 4 chain in registers, 5 groups of moves")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

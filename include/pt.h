@@ -226,11 +226,14 @@ int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, 
  * evaluated together; 2 = a CTA of 1-8 warps per replica (by N), one move at a time;
  * 3 = a CTA of 2-8 warps per replica, each warp evaluating one move of a group of moves with
  * distinct beads; 4 = one warp per replica with the chain in registers (N_max <= 1024),
- * taking double-float work only where a decision or an accepted dE needs it. Kernels 0-3
- * run the same chain, move for move, and differ only in the summation order of dE. Kernel
- * 4 takes each Metropolis decision whose dE lies outside its FP32 error bound of theta
- * exactly, so it runs that chain too except where a dE falls within the parity tolerance of
- * its threshold. PT_EINVAL for an unknown kernel or kernel 4 with N_max > 1024. */
+ * taking double-float work only where a decision or an accepted dE needs it; 5 = a CTA of
+ * 4-8 warps per replica with the chain in every warp's registers, each warp evaluating one
+ * move of a group of consecutive moves on distinct beads, decisions taken in move order
+ * (N_max <= 1024). Kernels 0-3 run the same chain, move for move, and differ only in the
+ * summation order of dE. Kernels 4 and 5 take each Metropolis decision whose dE lies
+ * outside its FP32 error bound of theta exactly, so they run that chain too except where a
+ * dE falls within the parity tolerance of its threshold (and 4 and 5 run the same chain).
+ * PT_EINVAL for an unknown kernel or kernel 4 or 5 with N_max > 1024. */
 int pt_set_sweep_kernel(pt_ctx* h, int variant);
 
 /* The kernel in use (creation picks one from the chain length; see pt_autotune). */

@@ -623,9 +623,9 @@ extern "C" int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every) {
 extern "C" int pt_set_sweep_kernel(pt_ctx* h, int variant) {
     int rc = check_usable(h);
     if (rc) return rc;
-    if (variant < kSweepSimple || variant > kSweepReg)
+    if (variant < kSweepSimple || variant > kSweepGrp)
         return fail(PT_EINVAL, "unknown sweep kernel %d", variant);
-    if (variant == kSweepReg && h->nmax > kRegMaxN)
+    if ((variant == kSweepReg || variant == kSweepGrp) && h->nmax > kRegMaxN)
         return fail(PT_EINVAL, "sweep kernel %d holds chains of at most %d beads", variant, kRegMaxN);
     if ((rc = sync_and_check(h))) return rc;
     const int warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, variant);
@@ -690,9 +690,9 @@ extern "C" int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen) 
     CK(h, cudaEventCreate(&b));
     int best = h->variant;
     float best_ms = 1e30f;
-    const int variants[] = {kSweepSimple, kSweepLookahead, kSweepTeam, kSweepWpm, kSweepReg};
+    const int variants[] = {kSweepSimple, kSweepLookahead, kSweepTeam, kSweepWpm, kSweepReg, kSweepGrp};
     for (int v : variants) {
-        if (v == kSweepReg && h->nmax > kRegMaxN) continue;
+        if ((v == kSweepReg || v == kSweepGrp) && h->nmax > kRegMaxN) continue;
         if ((rc = pt_set_sweep_kernel(h, v))) break;
         if ((rc = pt_sweep(h, 2, 1))) break;  // warm-up (and graph capture)
         CK(h, cudaEventRecord(a, h->stream));

@@ -71,11 +71,17 @@ struct State {
 // kSweepWpm gives each replica a CTA whose warps each evaluate one move of a group.
 // kSweepReg gives each replica one warp holding the chain in registers (N <= kRegMaxN) and
 // takes the double-float work only where a decision or an accepted energy needs it.
-enum : int { kSweepSimple = 0, kSweepLookahead = 1, kSweepTeam = 2, kSweepWpm = 3, kSweepReg = 4 };
+// kSweepGrp gives each replica a CTA of 4-8 warps holding the chain in registers, each warp
+// evaluating one move of a group of consecutive moves on distinct beads (N <= kRegMaxN).
+enum : int { kSweepSimple = 0, kSweepLookahead = 1, kSweepTeam = 2, kSweepWpm = 3, kSweepReg = 4, kSweepGrp = 5 };
 constexpr int kRegMaxN = 1024;
 int reg_slots(int nmax);
 size_t reg_smem_bytes(int nmax);
 cudaError_t launch_sweep_reg(const State& s, int chunk, cudaStream_t st);
+int grp_warps(int nmax);
+size_t grp_smem_bytes(int nmax, int warps);
+cudaError_t configure_sweep_grp(int nmax);
+cudaError_t launch_sweep_grp(const State& s, int chunk, cudaStream_t st);
 int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant);
 size_t sweep_smem_bytes(int nmax, int warps, int variant);
 cudaError_t configure_sweep(int nmax, int warps, int variant);  // per context, before any capture

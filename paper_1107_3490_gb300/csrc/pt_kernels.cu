@@ -949,6 +949,7 @@ __global__ void k_energy_final(const double* __restrict__ scratch, int n_conf, i
 // ---- launchers ----------------------------------------------------------------------------
 size_t sweep_smem_bytes(int nmax, int warps, int variant) {
     if (variant == kSweepReg) return reg_smem_bytes(nmax);
+    if (variant == kSweepGrp) return grp_smem_bytes(nmax, warps);
     if (variant == kSweepTeam) return team_smem_bytes(nmax, warps);
     if (variant == kSweepWpm) return wpm_smem_bytes(nmax, warps);
     const size_t per_warp = variant == kSweepLookahead ? la_warp_f4(nmax) : (size_t)nmax + (size_t)(nmax + 3) / 4;
@@ -962,6 +963,7 @@ int wpm_warps(int nmax) { return nmax <= 24 ? 2 : nmax <= 400 ? 4 : 8; }
 
 int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant) {
     if (variant == kSweepReg) return 1;
+    if (variant == kSweepGrp) return grp_warps(nmax);
     if (variant == kSweepTeam) return team_warps(nmax);
     if (variant == kSweepWpm) return wpm_warps(nmax);
     int w = 4;
@@ -974,6 +976,7 @@ int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant) {
 cudaError_t configure_sweep(int nmax, int warps, int variant) {
     const size_t smem = sweep_smem_bytes(nmax, warps, variant);
     if (variant == kSweepReg) return nmax <= kRegMaxN ? cudaSuccess : cudaErrorInvalidValue;
+    if (variant == kSweepGrp) return nmax <= kRegMaxN ? configure_sweep_grp(nmax) : cudaErrorInvalidValue;
     if (smem <= 48 * 1024) return cudaSuccess;
     if (variant == kSweepWpm) {
         const int a = (int)smem;
@@ -999,6 +1002,7 @@ cudaError_t configure_sweep(int nmax, int warps, int variant) {
 
 cudaError_t launch_sweep(const State& s, int chunk, int warps, int variant, cudaStream_t st) {
     if (variant == kSweepReg) return launch_sweep_reg(s, chunk, st);
+    if (variant == kSweepGrp) return launch_sweep_grp(s, chunk, st);
     const size_t smem = sweep_smem_bytes(s.nmax, warps, variant);
     if (variant == kSweepWpm) {
         switch (warps) {

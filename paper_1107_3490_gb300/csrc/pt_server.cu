@@ -189,7 +189,7 @@ cudaError_t make_pool(Pool& P, int nmax, int64_t reps, int64_t beads, int64_t bi
     for (int e = jobs - 1; e >= 0; --e) P.free_ens.push_back(e);
     // short chains: one warp per replica; longer: warp per move of a group
     P.variant = variant >= 0 ? variant : (nmax <= 64 ? kSweepSimple : kSweepWpm);
-    if (P.variant == kSweepReg && nmax > kRegMaxN) P.variant = kSweepWpm;  // register kernel: N <= 1024
+    if ((P.variant == kSweepReg || P.variant == kSweepGrp) && nmax > kRegMaxN) P.variant = kSweepWpm;  // N <= 1024
     P.warps = sweep_warps_per_block(nmax, (int)G, num_sms, P.variant);
     if (a == cudaSuccess) a = configure_sweep(nmax, P.warps, P.variant);
     return a;

@@ -1,0 +1,508 @@
+// pt_sweep_grp.cu -- group sweep: a CTA of W warps per replica evaluates up to W consecutive
+// moves at once, each warp one move, with the exact FP32 decisions of pt_sweep_reg.cu.
+//
+// The chain of a replica (Sec. 3.2) runs move after move; what lets several moves be
+// evaluated together is that consecutive moves on distinct beads interact only through the
+// pair terms between their own beads. For a group of moves m_0 < m_1 < ... on distinct
+// beads (the longest such run from each move is found once per batch), warp i evaluates
+// move m_i against the positions at the start of the group (every warp holds the whole
+// chain in registers): its row, its bonds, and the bracket of its dE from the exact
+// fixed-point sums of the lane bounds. Lane l < i of warp i forms the correction of move i
+// for an acceptance of move l: the term of move i's bead against bead k_l at its proposed
+// position minus the term against its old position (LJ, or FENE plus bonded LJ when the
+// beads are bonded), with its rounding bound. After one barrier warp 0 takes the decisions
+// in move order, one lane per move, adding for each accepted earlier move its correction
+// interval. A move whose threshold lies inside its interval ends the group; so does a move
+// whose value would rest on an inexact correction (a steep or bonded partner that moved):
+// it is evaluated again, against the updated chain, as the first move of the next group,
+// where an undecided move is decided on its value like kernel 4's. Then each accepted move
+// computes its dE value (double-float for steep row pairs and bonds far from r0), every
+// warp applies the accepted moves to its registers, and the chain in shared memory is
+// updated. The chain is therefore exactly that of pt_sweep_reg.cu, move for move.
+#include "pt_sweep_f32.cuh"
+
+namespace ptgb {
+
+namespace {
+
+// LJ term (Eqs. 1-2) of the move p -> pn against partner q in FP32 with its error bound:
+// the arithmetic of row_pass for one slot.
+struct PairF {
+    float t, e;
+    bool steep;
+};
+__device__ __forceinline__ PairF lj_pair_f32(float4 q, float3 p, float3 pn) {
+    const float dxo = __fsub_rn(q.x, p.x), dyo = __fsub_rn(q.y, p.y), dzo = __fsub_rn(q.z, p.z);
+    const float dxn = __fsub_rn(q.x, pn.x), dyn = __fsub_rn(q.y, pn.y), dzn = __fsub_rn(q.z, pn.z);
+    const float r2o = __fmaf_rn(dzo, dzo, __fmaf_rn(dyo, dyo, __fmul_rn(dxo, dxo)));
+    const float r2n = __fmaf_rn(dzn, dzn, __fmaf_rn(dyn, dyn, __fmul_rn(dxn, dxn)));
+    const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
+    const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
+    PairF r;
+    r.t = __fmul_rn(__fsub_rn(xn, xo), __fmaf_rn(kAf, __fadd_rn(xn, xo), -kBf));
+    const float w = __fadd_rn(fabsf(__fmul_rn(__fmaf_rn(2.f * kAf, xo, -kBf), xo)),
+                              fabsf(__fmul_rn(__fmaf_rn(2.f * kAf, xn, -kBf), xn)));
+    r.e = __fmaf_rn(kDeltaX, w, 4.f * kEps0 * fabsf(r.t));
+    r.steep = fminf(r2o, r2n) < kSteepTeam2f;
+    return r;
+}
+
+// Correction of a move (p -> pn) for an accepted move of a group partner from qo to qn:
+// term(qn) - term(qo), LJ or (bonded) FENE plus bonded LJ. Flags: bit 0 inexact (the
+// accurate value needs double-float), bit 1 undecidable (a bond at the FENE wall).
+__device__ __forceinline__ void correction_f32(float4 qo, float4 qn, float3 p, float3 pn, bool bonded, bool ljb,
+                                               float& d, float& e, unsigned& fl) {
+    if (bonded) {
+        // the difference of two FENE terms can cancel far below their size: its value is
+        // always taken in double-float (the bound still serves the decision)
+        const BondF a = bond_f32(qn, p, pn, ljb), b = bond_f32(qo, p, pn, ljb);
+        fl = 1u | ((a.edge || b.edge) ? 2u : 0u);
+        d = __fsub_rn(a.t, b.t);  // +inf when the new bond breaks
+        e = __fadd_ru(__fadd_ru(a.e, b.e), 2.f * kEps0 * fabsf(d) < __int_as_float(0x7f800000) ? 2.f * kEps0 * fabsf(d) : 0.f);
+    } else {
+        const PairF a = lj_pair_f32(qn, p, pn), b = lj_pair_f32(qo, p, pn);
+        fl = (a.steep || b.steep) ? 1u : 0u;
+        d = __fsub_rn(a.t, b.t);
+        e = __fadd_ru(__fadd_ru(a.e, b.e), 2.f * kEps0 * fabsf(d));
+    }
+}
+
+}  // namespace
+
+template <int W>
+__host__ __device__ constexpr size_t grp_fixed_bytes() {
+    return (size_t)(32 * W) * 2 * sizeof(float4)          // D0, D1
+           + (size_t)W * 2 * sizeof(float4)               // GP, GPN
+           + (size_t)W * 4 * sizeof(float)                // GL, GH, GV, GFL
+           + (size_t)W * W * 3 * sizeof(float)            // CD, CE, CFL
+           + 16;                                          // first-move decision
+}
+
+template <int U, int W>
+__global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
+    constexpr int T = 32 * W;  // threads, and moves per batch
+    extern __shared__ float4 smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = blockIdx.x;
+    if (g >= S.n_reps) return;  // whole CTA
+    const RepDev rd = S.reps[g];
+    const EnsDev ed = S.ens[rd.ens];
+    const int N = rd.N;
+    int64_t s = S.rep_sweep[g];
+    const int64_t s_end = min(ed.target, s + (int64_t)chunk);
+    if (s >= s_end) return;  // uniform over the CTA
+
+    float4* P = smem;                         // [nmax] chain at the start of the current group
+    float4* D0 = P + S.nmax;                  // [T] move: bead | batch bond flags << 16, displacement
+    float4* D1 = D0 + T;                      // [T] move: theta, batch bond terms, bound
+    float4* GP = D1 + T;                      // [W] group move i: old position (.w = bead bits)
+    float4* GPN = GP + W;                     // [W] proposed position
+    float* GL = reinterpret_cast<float*>(GPN + W);  // [W] lower bound of dE_i (NaN: none)
+    float* GH = GL + W;                       // [W] upper bound
+    float* GV = GH + W;                       // [W] value of dE_i (accepted / logged moves)
+    unsigned* GFL = reinterpret_cast<unsigned*>(GV + W);  // [W] flags of move i
+    float* CD = reinterpret_cast<float*>(GFL + W);        // [W][W] correction of move i for move l
+    float* CE = CD + W * W;                                // its bound
+    unsigned* CFL = reinterpret_cast<unsigned*>(CE + W * W);  // its flags
+    int* FIRST = reinterpret_cast<int*>(CFL + W * W);     // decision of an undecided first move
+    int* Q = FIRST + 4;                                    // [W][nmax] steep partners (refinement)
+    unsigned char* MOV = reinterpret_cast<unsigned char*>(Q + W * S.nmax);  // [nmax] moved in this batch
+
+    for (int i = tid; i < N; i += T) {
+        float4 q = S.pos[rd.pos_off + i];
+        q.w = 0.f;
+        P[i] = q;
+    }
+    __syncthreads();
+    float qx[U], qy[U], qz[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int j = lane + 32 * u;
+        const float4 q = j < N ? P[j] : make_float4(kFar, kFar, kFar, 0.f);
+        qx[u] = q.x;
+        qy[u] = q.y;
+        qz[u] = q.z;
+    }
+
+    double E = S.E[g];
+    const int slot = S.temp_of_rep[g];
+    const int gs = rd.slot_base + slot;
+    const float Tf = S.Tf[gs];
+    const uint32_t k0 = (uint32_t)ed.seed, k1 = (uint32_t)(ed.seed >> 32);
+    const uint32_t c3 = ed.ens_id | (kTagMove << 24);
+    const bool ljb = ed.lj_bonded != 0;
+    const float delta = ed.delta;
+    const float kInf = __int_as_float(0x7f800000);
+    const float kNaN = __int_as_float(0x7fffffff);
+    const float sum_err = (float)(U + 3) * kEps0;
+
+    for (; s < s_end; ++s) {
+        const bool logging = S.log_bead && s >= S.log_s0 && s < S.log_s0 + S.log_ns;
+        const size_t lrow = logging ? (size_t)(s - S.log_s0) * S.log_pstride + rd.pos_off : 0;
+        df dsum = {0.f, 0.f};
+        int nacc = 0;
+        for (int m0 = 0; m0 < N; m0 += T) {
+            // ---- batch: draws of move m0 + tid and its bond terms against the chain now
+            const int mc = min(T, N - m0);
+            __syncthreads();  // the previous batch's arrays are no longer read
+            for (int i = tid; i < N; i += T) MOV[i] = 0;
+            if (tid < mc) {
+                const uint32_t m = (uint32_t)(m0 + tid);
+                const u4 w4 = philox(u4{2u * m, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                const u4 v4 = philox(u4{2u * m + 1u, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
+                const int km = (int)__umulhi(w4.x, (uint32_t)N);
+                const float sx = __fsub_rn(__fmul_rn(2.f, unif24(w4.y)), 1.f);
+                const float sy = __fsub_rn(__fmul_rn(2.f, unif24(w4.z)), 1.f);
+                const float sz = __fsub_rn(__fmul_rn(2.f, unif24(w4.w)), 1.f);
+                const float th = __fmul_rn(-logf(unif24(v4.x)), Tf);
+                const float4 q = P[km];
+                const float3 pk = make_float3(q.x, q.y, q.z);
+                const float3 pnk = make_float3(__fadd_rn(q.x, __fmul_rn(delta, sx)), __fadd_rn(q.y, __fmul_rn(delta, sy)),
+                                               __fadd_rn(q.z, __fmul_rn(delta, sz)));
+                float bt = 0.f, be = 0.f;
+                unsigned bfl = 0u;
+                if (km > 0) {
+                    const BondF a = bond_f32(P[km - 1], pk, pnk, ljb);
+                    bt = a.t;
+                    be = a.e;
+                    bfl |= (a.inexact ? 1u : 0u) | (a.edge ? 2u : 0u);
+                }
+                if (km + 1 < N) {
+                    const BondF c = bond_f32(P[km + 1], pk, pnk, ljb);
+                    bt = __fadd_rn(bt, c.t);
+                    be = __fadd_rn(be, c.e);
+                    bfl |= (c.inexact ? 1u : 0u) | (c.edge ? 2u : 0u);
+                }
+                D0[tid] = make_float4(__int_as_float(km | (int)(bfl << 16)), sx, sy, sz);
+                D1[tid] = make_float4(th, bt, be, 0.f);
+            }
+            __syncthreads();
+            // group length from each move: the longest run of distinct beads (at most W)
+            if (tid < mc) {
+                int kb[W];
+                int len = 1;
+                bool stop = false;
+#pragma unroll
+                for (int j = 0; j < W; ++j) kb[j] = tid + j < mc ? (__float_as_int(D0[tid + j].x) & 0xffff) : -1 - j;
+#pragma unroll
+                for (int j = 1; j < W; ++j) {
+                    bool dup = tid + j >= mc;
+#pragma unroll
+                    for (int l = 0; l < j; ++l) dup |= kb[l] == kb[j];
+                    stop |= dup;
+                    if (!stop) len = j + 1;
+                }
+                D1[tid].w = __int_as_float(len);
+            }
+            __syncthreads();
+            for (int g0 = 0; g0 < mc;) {
+                const int w = __float_as_int(D1[g0].w);
+                // ---- warp i < w evaluates move g0 + i against the chain at group start
+                float part = 0.f, aord = 0.f, bnd = 0.f;
+                unsigned stm = 0u, mfl = 0u;
+                int k = 0;
+                float3 p = make_float3(0.f, 0.f, 0.f), pn = p;
+                float theta = 0.f;
+                if (warp < w) {
+                    const int i = warp;
+                    const float4 d0 = D0[g0 + i], d1 = D1[g0 + i];
+                    const int kw = __float_as_int(d0.x);
+                    k = kw & 0xffff;
+                    theta = d1.x;
+                    const float4 p4 = P[k];
+                    p = make_float3(p4.x, p4.y, p4.z);
+                    pn = make_float3(__fadd_rn(p.x, __fmul_rn(delta, d0.y)), __fadd_rn(p.y, __fmul_rn(delta, d0.z)),
+                                     __fadd_rn(p.z, __fmul_rn(delta, d0.w)));
+                    const RowSums rs = row_pass<U>(qx, qy, qz, p, pn, k, lane, N);
+                    aord = rs.aord;
+                    stm = rs.stm;
+                    float bnde = 0.f;
+                    unsigned bf = 0u;
+                    const bool stale = MOV[k] || (k > 0 && MOV[k - 1]) || (k + 1 < N && MOV[k + 1]);
+                    if (!stale) {
+                        if (lane == 0) {
+                            bnd = d1.y;
+                            bnde = d1.z;
+                            bf = (unsigned)kw >> 16;
+                        }
+                    } else if (lane < 2) {
+                        const int j = lane == 0 ? k - 1 : k + 1;
+                        if (j >= 0 && j < N) {
+                            const BondF x = bond_f32(P[j], p, pn, ljb);
+                            bnd = x.t;
+                            bnde = x.e;
+                            bf = (x.inexact ? 1u : 0u) | (x.edge ? 2u : 0u);
+                        }
+                    }
+                    part = __fadd_rn(__fadd_rn(rs.aord, rs.ast), bnd);
+                    const float bab = fabsf(bnd) < kInf ? fabsf(bnd) : 0.f;
+                    const float el = __fmaf_rn(kDeltaX, rs.sw, __fmaf_rn(sum_err, __fadd_rn(rs.sab, bab), bnde));
+                    const float lb = __fsub_rd(part, el), ub = __fadd_ru(part, el);
+                    const bool lo_bad = !(lb >= -kQMax) || (bf & 2u);
+                    const bool hi_bad = !(ub <= kQMax) || (bf & 2u);
+                    const int ql = lo_bad ? 0 : __float2int_rd(__fmul_rd(fminf(lb, kQMax), kQ));
+                    const int qh = hi_bad ? 0 : __float2int_ru(__fmul_ru(fmaxf(ub, -kQMax), kQ));
+                    const int sl = __reduce_add_sync(kFull, ql);
+                    const int sh = __reduce_add_sync(kFull, qh);
+                    mfl = __reduce_or_sync(kFull, (lo_bad ? 1u : 0u) | (hi_bad ? 2u : 0u) | (rs.stm ? 4u : 0u) |
+                                                      ((bf & 3u) ? 8u : 0u));
+                    // corrections for accepted earlier group moves: lane l < i
+                    if (lane < i) {
+                        const int l = lane;
+                        const float4 e0 = D0[g0 + l];
+                        const int kl = __float_as_int(e0.x) & 0xffff;
+                        const float4 qo = P[kl];
+                        const float4 qn = make_float4(__fadd_rn(qo.x, __fmul_rn(delta, e0.y)),
+                                                      __fadd_rn(qo.y, __fmul_rn(delta, e0.z)),
+                                                      __fadd_rn(qo.z, __fmul_rn(delta, e0.w)), 0.f);
+                        float d, e;
+                        unsigned cf;
+                        correction_f32(qo, qn, p, pn, kl - k == 1 || k - kl == 1, ljb, d, e, cf);
+                        CD[i * W + l] = d;
+                        CE[i * W + l] = e;
+                        CFL[i * W + l] = cf;
+                    }
+                    if (lane == 0) {
+                        GP[i] = make_float4(p.x, p.y, p.z, __int_as_float(k));
+                        GPN[i] = make_float4(pn.x, pn.y, pn.z, 0.f);
+                        GL[i] = (mfl & 1u) ? kNaN : __fmul_rd(__int2float_rd(sl), kQInv);
+                        GH[i] = (mfl & 2u) ? kNaN : __fmul_ru(__int2float_ru(sh), kQInv);
+                    }
+                }
+                __syncthreads();
+                // ---- warp 0 takes the decisions in move order, lane i holding move i
+                if (warp == 0) {
+                    const bool mine = lane < w;
+                    const float lo0 = mine ? GL[lane] : kNaN, hi0 = mine ? GH[lane] : kNaN;
+                    const float th = mine ? D1[g0 + lane].x : 0.f;
+                    float cd[W], ce[W];
+                    unsigned cf[W];
+#pragma unroll
+                    for (int l = 0; l < W; ++l) {
+                        const bool has = mine && l < lane;
+                        cd[l] = has ? CD[lane * W + l] : 0.f;
+                        ce[l] = has ? CE[lane * W + l] : 0.f;
+                        cf[l] = has ? CFL[lane * W + l] : 0u;
+                    }
+                    unsigned am = 0u;
+                    int n = w, by_value = 0;
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        if (i >= w) break;
+                        // every lane forms its own interval under the decisions so far; lane i's counts
+                        float lo = lo0, hi = hi0;
+                        bool ok_lo = lo0 == lo0, ok_hi = hi0 == hi0, cin = false;
+#pragma unroll
+                        for (int l = 0; l < W; ++l) {
+                            if (l < i && ((am >> l) & 1u)) {
+                                cin |= cf[l] != 0u;
+                                if ((cf[l] & 2u) || cd[l] != cd[l]) {
+                                    ok_lo = ok_hi = false;
+                                } else {
+                                    lo = __fsub_rd(__fadd_rd(lo, cd[l]), ce[l]);
+                                    hi = __fadd_ru(__fadd_ru(hi, cd[l]), ce[l]);
+                                }
+                            }
+                        }
+                        int dec = 2;  // 0 reject, 1 accept, 2 undecided
+                        if (ok_lo && lo >= th) dec = 0;
+                        else if (ok_hi && hi < th) dec = 1;
+                        // a value that would rest on an inexact correction: evaluate it afresh
+                        if (cin && (dec == 1 || logging)) dec = 2;
+                        dec = __shfl_sync(kFull, dec, i);
+                        if (dec == 2) {
+                            n = i;
+                            break;
+                        }
+                        if (dec == 1) am |= 1u << i;
+                    }
+                    if (n == 0) {
+                        // the first move undecided: its value decides (warp 0 evaluated it)
+                        float v;
+                        if (mfl & 12u) {
+                            float a2 = aord;
+                            if (mfl & 4u) {
+                                const int cnt = __popc(stm);
+                                int pre = cnt;
+#pragma unroll
+                                for (int o = 1; o < 32; o <<= 1) {
+                                    const int y = __shfl_up_sync(kFull, pre, o);
+                                    if (lane >= o) pre += y;
+                                }
+                                const int qn = __shfl_sync(kFull, pre, 31);
+                                int at = pre - cnt;
+                                for (unsigned m = stm; m; m &= m - 1) Q[at++] = lane + 32 * (__ffs(m) - 1);
+                                __syncwarp();
+                                a2 = __fadd_rn(a2, steep_pairs(Q, qn, P, p, pn, -1, make_float4(0.f, 0.f, 0.f, 0.f), lane));
+                            }
+                            float bacc = 0.f;
+                            if (lane < 2) {
+                                const int j = lane == 0 ? k - 1 : k + 1;
+                                if (j >= 0 && j < N) {
+                                    bool brk = false;
+                                    bacc = bond_term_team(P[j], p, pn, ljb, &brk);
+                                    if (brk) bacc = kInf;
+                                }
+                            }
+                            v = warp_sum(__fadd_rn(a2, bacc));
+                        } else {
+                            v = warp_sum(part);
+                        }
+                        am = v < theta ? 1u : 0u;  // NaN and +inf reject
+                        n = 1;
+                        by_value = 1;
+                        if (lane == 0) GV[0] = v;
+                    }
+                    if (lane == 0) {
+                        FIRST[0] = (int)am;
+                        FIRST[1] = n;
+                        FIRST[2] = by_value;
+                    }
+                }
+                __syncthreads();
+                const unsigned amask = (unsigned)FIRST[0];
+                const int nd = FIRST[1];
+                const bool value0_known = FIRST[2] != 0;  // move 0's value came with its decision
+                // ---- accepted moves into every warp's registers; values; the chain in smem
+                for (unsigned m = amask; m; m &= m - 1) {
+                    const int l = __ffs(m) - 1;
+                    const int kl = __float_as_int(GP[l].w);
+                    if (lane == (kl & 31)) {
+                        const float4 qn = GPN[l];
+                        const int su = kl >> 5;
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            if (u == su) {
+                                qx[u] = qn.x;
+                                qy[u] = qn.y;
+                                qz[u] = qn.z;
+                            }
+                    }
+                }
+                if (warp < nd) {
+                    const int i = warp;
+                    const bool acc_i = (amask >> i) & 1u;
+                    if ((acc_i || logging) && !(i == 0 && value0_known)) {
+                        float v;
+                        if (mfl & 12u) {
+                            // double-float for the steep row pairs and inexact bonds; the
+                            // corrections of accepted partners are exact FP32 terms here
+                            float a2 = aord;
+                            if (mfl & 4u) {
+                                const int cnt = __popc(stm);
+                                int pre = cnt;
+#pragma unroll
+                                for (int o = 1; o < 32; o <<= 1) {
+                                    const int y = __shfl_up_sync(kFull, pre, o);
+                                    if (lane >= o) pre += y;
+                                }
+                                const int qn = __shfl_sync(kFull, pre, 31);
+                                int* Qw = Q + warp * S.nmax;
+                                int at = pre - cnt;
+                                for (unsigned m = stm; m; m &= m - 1) Qw[at++] = lane + 32 * (__ffs(m) - 1);
+                                __syncwarp();
+                                a2 = __fadd_rn(a2, steep_pairs(Qw, qn, P, p, pn, -1, make_float4(0.f, 0.f, 0.f, 0.f), lane));
+                            }
+                            float bacc = 0.f;
+                            if (lane < 2) {
+                                const int j = lane == 0 ? k - 1 : k + 1;
+                                if (j >= 0 && j < N) {
+                                    bool brk = false;
+                                    bacc = bond_term_team(P[j], p, pn, ljb, &brk);
+                                    if (brk) bacc = kInf;
+                                }
+                            }
+                            v = warp_sum(__fadd_rn(a2, bacc));
+                        } else {
+                            v = warp_sum(part);
+                        }
+                        for (int l = 0; l < i; ++l)
+                            if ((amask >> l) & 1u) v = __fadd_rn(v, CD[i * W + l]);
+                        if (lane == 0) GV[i] = v;
+                    }
+                }
+                __syncthreads();
+                // ---- the chain in shared memory, the log, the energy sum
+                if (tid == 0)
+                    for (unsigned m = amask; m; m &= m - 1) {
+                        const int l = __ffs(m) - 1;
+                        const int kl = __float_as_int(GP[l].w);
+                        P[kl] = GPN[l];
+                        MOV[kl] = 1;
+                    }
+                if (logging && lane == 0 && warp < nd) {
+                    const size_t li = lrow + m0 + g0 + warp;
+                    S.log_bead[li] = __float_as_int(GP[warp].w);
+                    S.log_de[li] = GV[warp];
+                    S.log_theta[li] = D1[g0 + warp].x;
+                    S.log_acc[li] = (amask >> warp) & 1u;
+                }
+                for (unsigned m = amask; m; m &= m - 1) {
+                    dsum = df_add(dsum, df{GV[__ffs(m) - 1], 0.f});
+                    ++nacc;
+                }
+                __syncthreads();
+                g0 += nd;
+            }
+        }
+        E = (E + (double)dsum.hi) + (double)dsum.lo;
+        if (warp == 0) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += T) S.pos[rd.pos_off + i] = P[i];
+    if (tid == 0) {
+        S.E[g] = E;
+        S.rep_sweep[g] = s_end;
+    }
+}
+
+int grp_warps(int nmax) { return nmax <= 200 ? 4 : 8; }
+
+size_t grp_smem_bytes(int nmax, int warps) {
+    const size_t fixed = warps == 4 ? grp_fixed_bytes<4>() : grp_fixed_bytes<8>();
+    return (size_t)nmax * sizeof(float4) + fixed + (size_t)warps * nmax * sizeof(int) + (size_t)nmax + 16;
+}
+
+template <int W>
+static cudaError_t launch_grp_w(const State& s, int chunk, cudaStream_t st, size_t smem) {
+    switch (reg_slots(s.nmax)) {
+        case 1: k_sweep_grp<1, W><<<s.n_reps, 32 * W, smem, st>>>(s, chunk); break;
+        case 2: k_sweep_grp<2, W><<<s.n_reps, 32 * W, smem, st>>>(s, chunk); break;
+        case 4: k_sweep_grp<4, W><<<s.n_reps, 32 * W, smem, st>>>(s, chunk); break;
+        case 8: k_sweep_grp<8, W><<<s.n_reps, 32 * W, smem, st>>>(s, chunk); break;
+        case 16: k_sweep_grp<16, W><<<s.n_reps, 32 * W, smem, st>>>(s, chunk); break;
+        case 32: k_sweep_grp<32, W><<<s.n_reps, 32 * W, smem, st>>>(s, chunk); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t configure_grp_w(int smem) {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](auto kern) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    };
+    set(k_sweep_grp<1, W>);
+    set(k_sweep_grp<2, W>);
+    set(k_sweep_grp<4, W>);
+    set(k_sweep_grp<8, W>);
+    set(k_sweep_grp<16, W>);
+    set(k_sweep_grp<32, W>);
+    return e;
+}
+
+cudaError_t configure_sweep_grp(int nmax) {
+    const int w = grp_warps(nmax);
+    const size_t smem = grp_smem_bytes(nmax, w);
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return w == 4 ? configure_grp_w<4>((int)smem) : configure_grp_w<8>((int)smem);
+}
+
+cudaError_t launch_sweep_grp(const State& s, int chunk, cudaStream_t st) {
+    const int w = grp_warps(s.nmax);
+    const size_t smem = grp_smem_bytes(s.nmax, w);
+    return w == 4 ? launch_grp_w<4>(s, chunk, st, smem) : launch_grp_w<8>(s, chunk, st, smem);
+}
+
+}  // namespace ptgb

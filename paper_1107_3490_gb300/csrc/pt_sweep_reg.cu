@@ -26,122 +26,9 @@
 // evaluation of those terms exactly as the other sweep kernels do for every move. A move
 // inside the bracket takes that value and decides on it, like the other kernels. With the
 // per-move log on, every move computes the value it logs in the same way.
-#include "pt_sweep.cuh"
+#include "pt_sweep_f32.cuh"
 
 namespace ptgb {
-
-namespace {
-
-constexpr float kEps0 = 5.9604645e-08f;  // 2^-24
-constexpr float kDeltaX = 2.0e-6f;       // bound on the relative error of x = r^-6 in FP32
-constexpr float kFar = 1.0e18f;          // coordinate of an absent partner (r^2 stays finite)
-constexpr float kQ = 65536.f;            // fixed point of the decision sums: 2^-16 per unit
-constexpr float kQInv = 1.52587890625e-05f;
-constexpr float kQMax = 1000.f;          // lane bounds clamped to +-1000: 32 lanes fit in int32
-constexpr float kEdge = 1.0e-5f;         // bond lengths this close to the FENE wall: undecided
-
-// Bonded partner q of the moved bead in FP32: FENE (Eq. 3) plus, if lj, the LJ term, with a
-// bound e on the rounding error. inexact: the accurate value needs double-float (a bond
-// length at least 0.2 from r0, or a steep LJ term); edge: a bond length within kEdge of the
-// FENE wall, where FP32 cannot tell whether the bond breaks.
-struct BondF {
-    float t, e;
-    bool inexact, edge;
-};
-__device__ __forceinline__ BondF bond_f32(float4 q, float3 p, float3 pn, bool lj) {
-    const float R = (float)kRF;
-    BondF b = {0.f, 0.f, false, false};
-    const float r2o = r2_f32(q, p), r2n = r2_f32(q, pn);
-    const float ro = __fsqrt_rn(r2o), rn = __fsqrt_rn(r2n);
-    const float uo = __fsub_rn(ro, (float)kR0), un = __fsub_rn(rn, (float)kR0);
-    if (fabsf(un) > R + kEdge) {  // the bond breaks: E = +inf, the move is rejected
-        b.t = __int_as_float(0x7f800000);
-        return b;
-    }
-    const float umax = fmaxf(fabsf(uo), fabsf(un));
-    if (umax >= R - kEdge) {
-        b.edge = true;
-        return b;
-    }
-    b.inexact = umax >= kFeneUmaxF;
-    const float tf = fene_diff_f32(q, p, pn, r2o, r2n);
-    // first-order bound through the intermediates of fene_diff_f32 (same expressions)
-    const float dx = __fsub_rn(pn.x, p.x), dy = __fsub_rn(pn.y, p.y), dz = __fsub_rn(pn.z, p.z);
-    const float sx = __fsub_rn(__fmul_rn(2.f, __fsub_rn(q.x, p.x)), dx);
-    const float sy = __fsub_rn(__fmul_rn(2.f, __fsub_rn(q.y, p.y)), dy);
-    const float sz = __fsub_rn(__fmul_rn(2.f, __fsub_rn(q.z, p.z)), dz);
-    const float e_dr2 = 8.f * kEps0 * (fabsf(dx * sx) + fabsf(dy * sy) + fabsf(dz * sz) + dx * dx + dy * dy + dz * dz);
-    const float rsum = __fadd_rn(ro, rn);
-    const float drr = __fdividef(__fmaf_rn(dz, sz, __fmaf_rn(dy, sy, __fmul_rn(dx, sx))), rsum);
-    const float usum = __fadd_rn(uo, un);
-    const float wo = __fmul_rn(__fsub_rn(R, uo), __fadd_rn(R, uo));
-    const float z = __fdividef(__fmul_rn(drr, usum), wo);
-    const float e_u = 3.0e-7f;  // |r| error (rounded r^2 and sqrt) plus the float rounding of r0
-    const float e_drr = e_dr2 / rsum + fabsf(drr) * (2.f * e_u / rsum + 4.f * kEps0);
-    const float e_wo = 2.f * R * (e_u + 2.e-8f) + 4.f * kEps0 * wo;
-    const float e_z = (e_drr * fabsf(usum) + fabsf(drr) * (2.f * e_u + kEps0)) / wo + fabsf(z) * (e_wo / wo + 4.f * kEps0);
-    const float den = 1.f + z - e_z;
-    if (!(den > 0.05f)) {  // log1p too steep here for this simple bound
-        b.edge = true;
-        return b;
-    }
-    float e = 1.5f * (1.8f * e_z / den + 4.f * kEps0 * fabsf(tf)) + 1e-9f;
-    float t = tf;
-    if (lj) {
-        const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
-        const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
-        const float tl = lj_term_f32(r2o, r2n);
-        const float w = fabsf(xo * (2.f * kAf * xo - kBf)) + fabsf(xn * (2.f * kAf * xn - kBf));
-        e += kDeltaX * w + 4.f * kEps0 * fabsf(tl);
-        b.inexact |= fminf(r2o, r2n) < kSteepTeam2f;
-        t = __fadd_rn(t, tl);
-    }
-    b.t = t;
-    b.e = e + kEps0 * fabsf(t);
-    return b;
-}
-
-}  // namespace
-
-// Row of the moved bead k over this lane's partners: sums of the ordinary and of the steep
-// FP32 terms, of |t| and of the error weights |x_o (2 A x_o - B)| + |x_n (2 A x_n - B)|, and
-// the mask of slots holding a steep partner. Slot u holds bead lane + 32 u. Slots go in
-// groups of four without a branch inside a group, so that their dependency chains
-// interleave; a group wholly beyond N is skipped.
-struct RowSums {
-    float aord, ast, sab, sw;
-    unsigned stm;
-};
-template <int U>
-__device__ __forceinline__ RowSums row_pass(const float (&qx)[U], const float (&qy)[U], const float (&qz)[U],
-                                            float3 p, float3 pn, int k, int lane, int N) {
-    RowSums r = {0.f, 0.f, 0.f, 0.f, 0u};
-    const int kk = lane - k + 1;  // j - k + 1 for slot 0
-#pragma unroll
-    for (int u0 = 0; u0 < U; u0 += 4) {
-        if (u0 > 0 && 32 * u0 >= N) break;
-#pragma unroll
-        for (int u = u0; u < u0 + 4 && u < U; ++u) {
-            const float dxo = __fsub_rn(qx[u], p.x), dyo = __fsub_rn(qy[u], p.y), dzo = __fsub_rn(qz[u], p.z);
-            const float dxn = __fsub_rn(qx[u], pn.x), dyn = __fsub_rn(qy[u], pn.y), dzn = __fsub_rn(qz[u], pn.z);
-            const float r2o = __fmaf_rn(dzo, dzo, __fmaf_rn(dyo, dyo, __fmul_rn(dxo, dxo)));
-            const float r2n = __fmaf_rn(dzn, dzn, __fmaf_rn(dyn, dyn, __fmul_rn(dxn, dxn)));
-            const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
-            const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
-            const float t = __fmul_rn(__fsub_rn(xn, xo), __fmaf_rn(kAf, __fadd_rn(xn, xo), -kBf));
-            const float w = __fadd_rn(fabsf(__fmul_rn(__fmaf_rn(2.f * kAf, xo, -kBf), xo)),
-                                      fabsf(__fmul_rn(__fmaf_rn(2.f * kAf, xn, -kBf), xn)));
-            const bool use = (unsigned)(kk + 32 * u) > 2u;  // neither k nor bonded to k
-            const bool st = use && fminf(r2o, r2n) < kSteepTeam2f;
-            r.aord = __fadd_rn(r.aord, (use && !st) ? t : 0.f);
-            r.ast = __fadd_rn(r.ast, st ? t : 0.f);
-            r.sab = __fadd_rn(r.sab, use ? fabsf(t) : 0.f);
-            r.sw = __fadd_rn(r.sw, use ? w : 0.f);
-            r.stm |= st ? (1u << u) : 0u;
-        }
-    }
-    return r;
-}
 
 template <int U>
 __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {

@@ -15,7 +15,7 @@ from tests import parity
 pytestmark = pytest.mark.gpu
 
 KERNELS = {0: "one move at a time", 1: "lookahead groups", 2: "team of warps per replica",
-           3: "warp per move of a group", 4: "registers, deferred double-float"}
+           3: "warp per move of a group", 4: "registers, deferred double-float", 5: "groups of moves, registers"}
 
 
 @pytest.fixture(params=sorted(KERNELS), ids=lambda v: f"kernel{v}")

@@ -206,16 +206,21 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     made = ensemble_params(rank)
     h = pt.pt_create_batch([p for p, _ in made], stream.cuda_stream)
-    if args.kernel < 0:
-        kernel = pt.pt_autotune(h, 16)  # untimed; the chain state is restored afterwards
-    else:
-        kernel = args.kernel
-        pt.pt_set_sweep_kernel(h, kernel)
-    pt.pt_set_kernel_timing(h, True)
+    if args.kernel >= 0:
+        pt.pt_set_sweep_kernel(h, args.kernel)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB of L2
 
     for _ in range(args.warmup):
         pt.pt_sweep(h, SWEEPS_PER_STEP, 1)
+    if args.kernel < 0:
+        # untimed, on the warmed-up chain (the state is restored afterwards), then one more
+        # warm-up step with the chosen kernel
+        kernel = pt.pt_autotune(h, 100, force=True)
+        pt.pt_sweep(h, SWEEPS_PER_STEP, 1)
+    else:
+        kernel = args.kernel
+    pt.pt_set_kernel_timing(h, True)
+    pt.pt_sweep(h, 64, 1)
     pt.pt_sync(h)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -362,6 +367,8 @@ def run_served(args):
             for j in jobs]
     cfg = pt.pt_server_config_init(1000, 6 << 30)
     cfg.round_sweeps = 32
+    if args.kernel >= 0:
+        cfg.sweep_kernel = args.kernel
     srv = pt.pt_server_create(cfg)
     ids = [0] * n_jobs
     t_start = time.perf_counter()
@@ -397,7 +404,7 @@ def run_served(args):
             "data": "synthetic", "dtype": "f32",
             "config": {"workload": f"{n_jobs} PT jobs, Poisson arrivals {args.rate}/s, N log-uniform 20-1000, "
                                    "replicas uniform 16-128, budgets log-uniform 100-1000 sweeps, exchange every "
-                                   "sweep; server N_max 1000", "sweep_kernel": "k_sweep_wpm (chosen from N_max)"},
+                                   "sweep; server N_max 1000", "sweep_kernel": "k_sweep_team (the server default)"},
             "latency_s": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                           "max": lat[-1]},
             "makespan_s": makespan,

@@ -220,7 +220,7 @@ int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonde
 int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, double* out,
                            void* stream);
 
-/* Choose the sweep kernel (creation picks 0 below 50 beads, 4 up to 250, else 3):
+/* Choose the sweep kernel (creation picks 0 below 24 beads, 4 up to 96, 5 up to 1024, else 3):
  * 0 = one warp per replica, one move at a time;
  * 1 = one warp per replica, groups of up to 8 consecutive moves with distinct beads
  * evaluated together; 2 = a CTA of 1-8 warps per replica (by N), one move at a time;
@@ -278,8 +278,9 @@ typedef struct pt_server_config {
     int32_t job_capacity;     /* jobs resident at once                                    */
     int32_t round_sweeps;     /* sweeps per scheduling round (64)                         */
     int32_t threaded;         /* 1: a host thread runs the rounds; 0: pt_server_step      */
-    int32_t sweep_kernel;     /* -1: chosen from N_max; else as pt_set_sweep_kernel (4 on  */
-                              /* a class above 1024 beads runs kernel 3)                  */
+    int32_t sweep_kernel;     /* -1: kernel 2 (team, best when loaded); else as           */
+                              /* pt_set_sweep_kernel (4 or 5 on a class above 1024 beads   */
+                              /* runs kernel 3)                                           */
 } pt_server_config;
 
 /* Capacities for jobs of up to N_max beads in mem_budget_bytes of device memory. */

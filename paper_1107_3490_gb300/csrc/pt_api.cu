@@ -265,7 +265,9 @@ void drop_graph(pt_ctx* h) {
 // Kernel choice before any tuning, from timings on GB300 (4 x 64 replicas up to N = 300,
 // 128 replicas above): one warp per replica wins for short chains, the warp-per-move
 // lookahead from about 50 beads on.
-int default_variant(int nmax) { return nmax < 50 ? kSweepSimple : nmax <= 250 ? kSweepReg : kSweepWpm; }
+int default_variant(int nmax) {
+    return nmax < 24 ? kSweepSimple : nmax <= 96 ? kSweepReg : nmax <= kRegMaxN ? kSweepGrp : kSweepWpm;
+}
 
 pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     g_err.clear();

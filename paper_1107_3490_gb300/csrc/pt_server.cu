@@ -188,7 +188,10 @@ cudaError_t make_pool(Pool& P, int nmax, int64_t reps, int64_t beads, int64_t bi
     P.bins = Ranges(bins);
     for (int e = jobs - 1; e >= 0; --e) P.free_ens.push_back(e);
     // short chains: one warp per replica; longer: warp per move of a group
-    P.variant = variant >= 0 ? variant : (nmax <= 64 ? kSweepSimple : kSweepWpm);
+    // A loaded server is throughput-bound (many replicas in flight), where the team kernel
+    // measured best (200 Poisson jobs, N 20-1000: 2.54e8 updates/s against 2.27e8-2.45e8
+    // for kernels 3-5, also the lowest p50 / p99 latency).
+    P.variant = variant >= 0 ? variant : kSweepTeam;
     if ((P.variant == kSweepReg || P.variant == kSweepGrp) && nmax > kRegMaxN) P.variant = kSweepWpm;  // N <= 1024
     P.warps = sweep_warps_per_block(nmax, (int)G, num_sms, P.variant);
     if (a == cudaSuccess) a = configure_sweep(nmax, P.warps, P.variant);

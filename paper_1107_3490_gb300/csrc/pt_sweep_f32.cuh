@@ -120,4 +120,70 @@ __device__ __forceinline__ RowSums row_pass(const float (&qx)[U], const float (&
     return r;
 }
 
+// The accurate dE of a move (all lanes of the warp call it): the ordinary FP32 row terms
+// (aord, per lane), the steep pairs (slot mask stm) in double-float through a queue in
+// shared memory, and the bonds, recomputed with double-float where they are far from r0
+// when redo_bonds is set (else the FP32 bond share bnd stands). Out of line: it is the rare
+// path, and keeping it out of the sweep loop keeps that loop small.
+static __device__ __noinline__ float move_value_accurate(const float4* P, int* Q, int N, int k, float3 p, float3 pn, bool ljb,
+                                                  float aord, unsigned stm, bool steep, bool redo_bonds, float bnd,
+                                                  int lane) {
+    float a2 = aord;
+    if (steep) {
+        const int cnt = __popc(stm);
+        int pre = cnt;  // inclusive prefix of the steep counts over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, pre, o);
+            if (lane >= o) pre += y;
+        }
+        const int qn = __shfl_sync(kFull, pre, 31);
+        int at = pre - cnt;
+        for (unsigned m = stm; m; m &= m - 1) Q[at++] = lane + 32 * (__ffs(m) - 1);
+        __syncwarp();
+        a2 = __fadd_rn(a2, steep_pairs(Q, qn, P, p, pn, -1, make_float4(0.f, 0.f, 0.f, 0.f), lane));
+    }
+    float bacc = bnd;
+    if (redo_bonds) {
+        bacc = 0.f;
+        if (lane < 2) {
+            const int j = lane == 0 ? k - 1 : k + 1;
+            if (j >= 0 && j < N) {
+                bool brk = false;
+                bacc = bond_term_team(P[j], p, pn, ljb, &brk);
+                if (brk) bacc = __int_as_float(0x7f800000);
+            }
+        }
+    }
+    const float v = warp_sum(__fadd_rn(a2, bacc));
+    __syncwarp();  // the queue is read before the caller's next move writes it
+    return v;
+}
+
+// Deferred accurate terms. An accepted move whose dE the decision did not need exactly
+// enters the energy with its FP32 value; each of its inexact terms (a steep pair, a bond far
+// from r0) is recorded with the positions it was evaluated at, and later the warp adds
+// accurate - FP32 for all of them at once. Entry: partner q (.w = kind, 0 = none), old p,
+// new pn.
+constexpr int kPend = 64;                 // entries per warp
+constexpr float kPendLJ = 1.f, kPendBond = 2.f, kPendBondLJ = 3.f;
+
+// Sum over the pending entries of (accurate - FP32) value, in every lane.
+static __device__ __noinline__ float pending_correction(const float4* PE, int n, int lane) {
+    float c = 0.f;
+    for (int e = lane; e < n; e += 32) {
+        const float4 q = PE[3 * e], a = PE[3 * e + 1], b = PE[3 * e + 2];
+        const float3 p = make_float3(a.x, a.y, a.z), pn = make_float3(b.x, b.y, b.z);
+        if (q.w == kPendLJ) {
+            c = __fadd_rn(c, __fsub_rn(lj_diff_df(q, p, pn), lj_term_f32(r2_f32(q, p), r2_f32(q, pn))));
+        } else if (q.w != 0.f) {  // 0: an absent bond (chain end)
+            const bool lj = q.w == kPendBondLJ;
+            bool brk = false;
+            const float acc = bond_term_team(q, p, pn, lj, &brk);
+            c = __fadd_rn(c, __fsub_rn(acc, bond_f32(q, p, pn, lj).t));
+        }
+    }
+    return warp_sum(c);
+}
+
 }  // namespace ptgb

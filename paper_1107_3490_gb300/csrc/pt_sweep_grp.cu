@@ -16,9 +16,9 @@
 // whose value would rest on an inexact correction (a steep or bonded partner that moved):
 // it is evaluated again, against the updated chain, as the first move of the next group,
 // where an undecided move is decided on its value like kernel 4's. Then each accepted move
-// computes its dE value (double-float for steep row pairs and bonds far from r0), every
-// warp applies the accepted moves to its registers, and the chain in shared memory is
-// updated. The chain is therefore exactly that of pt_sweep_reg.cu, move for move.
+// takes its FP32 dE value (the double-float remainder of its steep row pairs and bonds far
+// from r0 is added at the end of the sweep, as in kernel 4), every warp applies the accepted
+// moves to its registers, and the chain in shared memory is updated. The chain is therefore exactly that of pt_sweep_reg.cu, move for move.
 #include "pt_sweep_f32.cuh"
 
 namespace ptgb {
@@ -105,8 +105,12 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
     float* CE = CD + W * W;                                // its bound
     unsigned* CFL = reinterpret_cast<unsigned*>(CE + W * W);  // its flags
     int* FIRST = reinterpret_cast<int*>(CFL + W * W);     // decision of an undecided first move
-    int* Q = FIRST + 4;                                    // [W][nmax] steep partners (refinement)
+    float* CW = reinterpret_cast<float*>(FIRST + 4);       // [W] deferred corrections of a sweep
+    float4* PE = reinterpret_cast<float4*>(CW + 4 * ((W + 3) / 4)) + warp * 3 * kPend;  // this warp's
+    int* Q = reinterpret_cast<int*>(reinterpret_cast<float4*>(CW + 4 * ((W + 3) / 4)) + W * 3 * kPend);
     unsigned char* MOV = reinterpret_cast<unsigned char*>(Q + W * S.nmax);  // [nmax] moved in this batch
+    int npend = 0;    // this warp's deferred accurate terms
+    float cw = 0.f;   // and the corrections already summed
 
     for (int i = tid; i < N; i += T) {
         float4 q = S.pos[rd.pos_off + i];
@@ -384,7 +388,44 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                     const bool acc_i = (amask >> i) & 1u;
                     if ((acc_i || logging) && !(i == 0 && value0_known)) {
                         float v;
-                        if (mfl & 12u) {
+                        if ((mfl & 12u) && !logging) {
+                            // a certain acceptance: its FP32 dE now, the accurate remainder of
+                            // its steep pairs and bonds (partners at group start, unmoved in
+                            // the group) at the end of the sweep
+                            v = warp_sum(part);
+                            const int cnt = __popc(stm);
+                            int pre = cnt;
+#pragma unroll
+                            for (int o = 1; o < 32; o <<= 1) {
+                                const int y = __shfl_up_sync(kFull, pre, o);
+                                if (lane >= o) pre += y;
+                            }
+                            const int tot = __shfl_sync(kFull, pre, 31) + ((mfl & 8u) ? 2 : 0);
+                            if (npend + tot > kPend) {
+                                cw = __fadd_rn(cw, pending_correction(PE, npend, lane));
+                                npend = 0;
+                                __syncwarp();
+                            }
+                            int at = npend + pre - cnt;
+                            for (unsigned m = stm; m; m &= m - 1) {
+                                const float4 q = P[lane + 32 * (__ffs(m) - 1)];
+                                PE[3 * at] = make_float4(q.x, q.y, q.z, kPendLJ);
+                                PE[3 * at + 1] = make_float4(p.x, p.y, p.z, 0.f);
+                                PE[3 * at + 2] = make_float4(pn.x, pn.y, pn.z, 0.f);
+                                ++at;
+                            }
+                            if ((mfl & 8u) && lane < 2) {
+                                const int j = lane == 0 ? k - 1 : k + 1;
+                                const int e = npend + tot - 2 + lane;
+                                const bool ok = j >= 0 && j < N;  // no entry beyond a chain end
+                                const float4 q = ok ? P[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                                PE[3 * e] = make_float4(q.x, q.y, q.z, ok ? (ljb ? kPendBondLJ : kPendBond) : 0.f);
+                                PE[3 * e + 1] = make_float4(p.x, p.y, p.z, 0.f);
+                                PE[3 * e + 2] = make_float4(pn.x, pn.y, pn.z, 0.f);
+                            }
+                            npend += tot;
+                            __syncwarp();
+                        } else if (mfl & 12u) {
                             // double-float for the steep row pairs and inexact bonds; the
                             // corrections of accepted partners are exact FP32 terms here
                             float a2 = aord;
@@ -445,6 +486,13 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                 g0 += nd;
             }
         }
+        // the deferred corrections of every warp, added in warp order
+        if (npend > 0) cw = __fadd_rn(cw, pending_correction(PE, npend, lane));
+        npend = 0;
+        if (lane == 0) CW[warp] = cw;
+        cw = 0.f;
+        __syncthreads();
+        for (int w2 = 0; w2 < W; ++w2) dsum = df_add(dsum, df{CW[w2], 0.f});
         E = (E + (double)dsum.hi) + (double)dsum.lo;
         if (warp == 0) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
     }
@@ -460,7 +508,8 @@ int grp_warps(int nmax) { return nmax <= 200 ? 4 : 8; }
 
 size_t grp_smem_bytes(int nmax, int warps) {
     const size_t fixed = warps == 4 ? grp_fixed_bytes<4>() : grp_fixed_bytes<8>();
-    return (size_t)nmax * sizeof(float4) + fixed + (size_t)warps * nmax * sizeof(int) + (size_t)nmax + 16;
+    return (size_t)nmax * sizeof(float4) + fixed + 4 * sizeof(float) * ((warps + 3) / 4) +
+           (size_t)warps * 3 * kPend * sizeof(float4) + (size_t)warps * nmax * sizeof(int) + (size_t)nmax + 16;
 }
 
 template <int W>

@@ -46,7 +46,9 @@ __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
     float4* P = smem;                                  // [nmax] the chain
     float4* D0 = P + S.nmax;                           // [32] move: bead | bond flags << 16, displacement
     float4* D1 = D0 + 32;                              // [32] move: theta, bond terms, bound, conflicts
-    int* Q = reinterpret_cast<int*>(D1 + 32);          // [nmax] steep partners of a refined move
+    float4* PE = D1 + 32;                              // [kPend][3] deferred accurate terms
+    int* Q = reinterpret_cast<int*>(PE + 3 * kPend);   // [nmax] steep partners of a refined move
+    int npend = 0;
     float qx[U], qy[U], qz[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -185,39 +187,49 @@ __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
                 }
                 float dE = 0.f;
                 if (accept || !sure || logging) {
-                    if (fl & 12u) {
+                    if ((fl & 12u) && (!sure || logging)) {
                         // the accurate value: steep pairs and inexact bonds in double-float
-                        float a2 = rs.aord;
-                        if (fl & 4u) {
+                        dE = move_value_accurate(P, Q, N, k, p, pn, ljb, rs.aord, rs.stm, (fl & 4u) != 0,
+                                                 (fl & 8u) != 0, bnd, lane);
+                    } else {
+                        dE = warp_sum(part);
+                        if (fl & 12u) {
+                            // a certain acceptance: its FP32 dE now, the accurate remainder of
+                            // its steep pairs and bonds later (pending_correction)
                             const int cnt = __popc(rs.stm);
-                            int pre = cnt;  // inclusive prefix of the steep counts over the lanes
+                            int pre = cnt;
 #pragma unroll
                             for (int o = 1; o < 32; o <<= 1) {
                                 const int y = __shfl_up_sync(kFull, pre, o);
                                 if (lane >= o) pre += y;
                             }
-                            const int qn = __shfl_sync(kFull, pre, 31);
-                            int at = pre - cnt;
-                            for (unsigned m = rs.stm; m; m &= m - 1) Q[at++] = lane + 32 * (__ffs(m) - 1);
-                            __syncwarp();
-                            a2 = __fadd_rn(a2, steep_pairs(Q, qn, P, p, pn, -1, pN, lane));
-                        }
-                        float bacc = bnd;
-                        if (fl & 8u) {
-                            bacc = 0.f;
-                            if (lane < 2) {
-                                const int j = lane == 0 ? k - 1 : k + 1;
-                                if (j >= 0 && j < N) {
-                                    bool brk = false;
-                                    bacc = bond_term_team(P[j], p, pn, ljb, &brk);
-                                    if (brk) bacc = kInf;
-                                }
+                            const int tot = __shfl_sync(kFull, pre, 31) + ((fl & 8u) ? 2 : 0);
+                            if (npend + tot > kPend) {
+                                const float c = pending_correction(PE, npend, lane);
+                                dsum = df_add(dsum, df{c, 0.f});
+                                npend = 0;
+                                __syncwarp();
                             }
+                            int at = npend + pre - cnt;
+                            for (unsigned m = rs.stm; m; m &= m - 1) {
+                                const float4 q = P[lane + 32 * (__ffs(m) - 1)];
+                                PE[3 * at] = make_float4(q.x, q.y, q.z, kPendLJ);
+                                PE[3 * at + 1] = make_float4(p.x, p.y, p.z, 0.f);
+                                PE[3 * at + 2] = make_float4(pn.x, pn.y, pn.z, 0.f);
+                                ++at;
+                            }
+                            if ((fl & 8u) && lane < 2) {
+                                const int j = lane == 0 ? k - 1 : k + 1;
+                                const int e = npend + tot - 2 + lane;
+                                const bool ok = j >= 0 && j < N;  // no entry beyond a chain end
+                                const float4 q = ok ? P[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                                PE[3 * e] = make_float4(q.x, q.y, q.z, ok ? (ljb ? kPendBondLJ : kPendBond) : 0.f);
+                                PE[3 * e + 1] = make_float4(p.x, p.y, p.z, 0.f);
+                                PE[3 * e + 2] = make_float4(pn.x, pn.y, pn.z, 0.f);
+                            }
+                            npend += tot;
+                            __syncwarp();
                         }
-                        dE = warp_sum(__fadd_rn(a2, bacc));
-                        __syncwarp();  // the queue is read before the next move writes it
-                    } else {
-                        dE = warp_sum(part);
                     }
                     if (!sure) accept = dE < theta;  // NaN and +inf reject
                 }
@@ -248,6 +260,12 @@ __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
                 __syncwarp();
             }
         }
+        if (npend > 0) {
+            const float c = pending_correction(PE, npend, lane);
+            dsum = df_add(dsum, df{c, 0.f});
+            npend = 0;
+            __syncwarp();
+        }
         E = (E + (double)dsum.hi) + (double)dsum.lo;
         sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
     }
@@ -265,7 +283,9 @@ int reg_slots(int nmax) {
     return u;
 }
 
-size_t reg_smem_bytes(int nmax) { return (size_t)nmax * (sizeof(float4) + sizeof(int)) + 64 * sizeof(float4); }
+size_t reg_smem_bytes(int nmax) {
+    return (size_t)nmax * (sizeof(float4) + sizeof(int)) + (64 + 3 * kPend) * sizeof(float4);
+}
 
 cudaError_t launch_sweep_reg(const State& s, int chunk, cudaStream_t st) {
     const size_t smem = reg_smem_bytes(s.nmax);

@@ -61,7 +61,7 @@ def test_served_job_matches_a_standalone_context():
         pt.pt_server_destroy(s)
     h = pt.pt_create_ex(p)
     try:
-        pt.pt_set_sweep_kernel(h, 0)  # the kernel of the server's class for chains up to 64 beads
+        pt.pt_set_sweep_kernel(h, 2)  # the server's kernel
         pt.pt_sweep(h, 100, 1)
         e_ctx, h_ctx = pt.pt_energies(h), pt.pt_histograms(h).reshape(8, 64)
     finally:

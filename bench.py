@@ -33,6 +33,10 @@ METRIC = "single-bead Metropolis updates/sec (all replicas)"
 KERNEL_NAMES = {0: "k_sweep", 1: "k_sweep_la", 2: "k_sweep_team", 3: "k_sweep_wpm", 4: "k_sweep_reg",
                 5: "k_sweep_grp"}
 UNIT = "updates/s"
+# DRAM bytes read + written per sweep launch on this workload (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum, one capture of the kernel as it stands); kernels without a current
+# capture report null
+TRAFFIC_BYTES = {"k_sweep_grp": 648704, "k_sweep_reg": 637184}
 WORKLOAD = (f"PT polymer N={N_BEADS} beads, {N_REP} replicas at T geometric {T_MIN}-{T_MAX}, "
             f"{N_ENS} ensembles (seeds 1-{N_ENS}) per GPU, delta 0.3, exchange every sweep, "
             f"FP64 recompute every 1000 sweeps, 4096 FP64 bins/slot; 1 step = {SWEEPS_PER_STEP} sweeps")
@@ -268,7 +272,8 @@ def run_gpu(args):
     achieved = pairs_per_launch * FLOPS_PER_PAIR / (kernel_ms / 1e3) / 1e12
     peak = fp32_peak_tflops(num_sms, 2070.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": KERNEL_NAMES[kernel], "launch_ms": kernel_ms, "launches_sampled": kernel_n,
+                "traffic": TRAFFIC_BYTES.get(KERNEL_NAMES[kernel]), "kernel": KERNEL_NAMES[kernel],
+                "launch_ms": kernel_ms, "launches_sampled": kernel_n,
                 "peak_basis": f"{num_sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)"}
     if clocks and clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / fp32_peak_tflops(num_sms, clocks["sm_mhz"])

@@ -105,9 +105,9 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
     float* CE = CD + W * W;                                // its bound
     unsigned* CFL = reinterpret_cast<unsigned*>(CE + W * W);  // its flags
     int* FIRST = reinterpret_cast<int*>(CFL + W * W);     // decision of an undecided first move
-    float* CW = reinterpret_cast<float*>(FIRST + 4);       // [W] deferred corrections of a sweep
-    float4* PE = reinterpret_cast<float4*>(CW + 4 * ((W + 3) / 4)) + warp * 3 * kPend;  // this warp's
-    int* Q = reinterpret_cast<int*>(reinterpret_cast<float4*>(CW + 4 * ((W + 3) / 4)) + W * 3 * kPend);
+    float* CW = reinterpret_cast<float*>(FIRST + 4);       // [W][4] per-warp sums of a sweep
+    float4* PE = reinterpret_cast<float4*>(CW + 4 * W) + warp * 3 * kPend;  // this warp's pending terms
+    int* Q = reinterpret_cast<int*>(reinterpret_cast<float4*>(CW + 4 * W) + W * 3 * kPend);
     unsigned char* MOV = reinterpret_cast<unsigned char*>(Q + W * S.nmax);  // [nmax] moved in this batch
     int npend = 0;    // this warp's deferred accurate terms
     float cw = 0.f;   // and the corrections already summed
@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
     for (; s < s_end; ++s) {
         const bool logging = S.log_bead && s >= S.log_s0 && s < S.log_s0 + S.log_ns;
         const size_t lrow = logging ? (size_t)(s - S.log_s0) * S.log_pstride + rd.pos_off : 0;
-        df dsum = {0.f, 0.f};
-        int nacc = 0;
+        df dsum = {0.f, 0.f}, wdsum = {0.f, 0.f};  // the sweep's sum; this warp's accepted moves
+        int nacc = 0, wnacc = 0;
         for (int m0 = 0; m0 < N; m0 += T) {
             // ---- batch: draws of move m0 + tid and its bond terms against the chain now
             const int mc = min(T, N - m0);
@@ -274,8 +274,11 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                     }
                 }
                 __syncthreads();
-                // ---- warp 0 takes the decisions in move order, lane i holding move i
-                if (warp == 0) {
+                // ---- every warp takes the decisions in move order, lane i holding move i; all
+                // warps read the same shared results, so they take the same decisions
+                unsigned amask = 0u;
+                int nd = w;
+                {
                     const bool mine = lane < w;
                     const float lo0 = mine ? GL[lane] : kNaN, hi0 = mine ? GH[lane] : kNaN;
                     const float th = mine ? D1[g0 + lane].x : 0.f;
@@ -288,8 +291,6 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                         ce[l] = has ? CE[lane * W + l] : 0.f;
                         cf[l] = has ? CFL[lane * W + l] : 0u;
                     }
-                    unsigned am = 0u;
-                    int n = w, by_value = 0;
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
                         if (i >= w) break;
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                         bool ok_lo = lo0 == lo0, ok_hi = hi0 == hi0, cin = false;
 #pragma unroll
                         for (int l = 0; l < W; ++l) {
-                            if (l < i && ((am >> l) & 1u)) {
+                            if (l < i && ((amask >> l) & 1u)) {
                                 cin |= cf[l] != 0u;
                                 if ((cf[l] & 2u) || cd[l] != cd[l]) {
                                     ok_lo = ok_hi = false;
@@ -315,13 +316,16 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                         if (cin && (dec == 1 || logging)) dec = 2;
                         dec = __shfl_sync(kFull, dec, i);
                         if (dec == 2) {
-                            n = i;
+                            nd = i;
                             break;
                         }
-                        if (dec == 1) am |= 1u << i;
+                        if (dec == 1) amask |= 1u << i;
                     }
-                    if (n == 0) {
-                        // the first move undecided: its value decides (warp 0 evaluated it)
+                }
+                bool value0_known = false;
+                if (nd == 0) {
+                    // the first move undecided: warp 0, which evaluated it, decides on its value
+                    if (warp == 0) {
                         float v;
                         if (mfl & 12u) {
                             float a2 = aord;
@@ -352,22 +356,17 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                         } else {
                             v = warp_sum(part);
                         }
-                        am = v < theta ? 1u : 0u;  // NaN and +inf reject
-                        n = 1;
-                        by_value = 1;
-                        if (lane == 0) GV[0] = v;
+                        if (lane == 0) {
+                            GV[0] = v;
+                            FIRST[0] = v < theta ? 1 : 0;  // NaN and +inf reject
+                        }
                     }
-                    if (lane == 0) {
-                        FIRST[0] = (int)am;
-                        FIRST[1] = n;
-                        FIRST[2] = by_value;
-                    }
+                    __syncthreads();
+                    amask = (unsigned)FIRST[0];
+                    nd = 1;
+                    value0_known = true;
                 }
-                __syncthreads();
-                const unsigned amask = (unsigned)FIRST[0];
-                const int nd = FIRST[1];
-                const bool value0_known = FIRST[2] != 0;  // move 0's value came with its decision
-                // ---- accepted moves into every warp's registers; values; the chain in smem
+                // ---- accepted moves into every warp's registers
                 for (unsigned m = amask; m; m &= m - 1) {
                     const int l = __ffs(m) - 1;
                     const int kl = __float_as_int(GP[l].w);
@@ -383,11 +382,17 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                             }
                     }
                 }
+                // ---- each warp: its move's value, its log entry, its smem position. Without the
+                // log only accepted moves take values, and no accepted move reads the smem
+                // position of a group partner that moved here: a partner it interacts with
+                // inexactly (steep or bonded) would have ended the group.
                 if (warp < nd) {
                     const int i = warp;
                     const bool acc_i = (amask >> i) & 1u;
-                    if ((acc_i || logging) && !(i == 0 && value0_known)) {
-                        float v;
+                    float v = 0.f;
+                    if (i == 0 && value0_known) {
+                        v = GV[0];
+                    } else if (acc_i || logging) {
                         if ((mfl & 12u) && !logging) {
                             // a certain acceptance: its FP32 dE now, the accurate remainder of
                             // its steep pairs and bonds (partners at group start, unmoved in
@@ -459,40 +464,50 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                         }
                         for (int l = 0; l < i; ++l)
                             if ((amask >> l) & 1u) v = __fadd_rn(v, CD[i * W + l]);
-                        if (lane == 0) GV[i] = v;
+                    }
+                    if (acc_i) {
+                        wdsum = df_add(wdsum, df{v, 0.f});
+                        ++wnacc;
+                    }
+                    if (lane == 0) {
+                        if (logging) {
+                            const size_t li = lrow + m0 + g0 + i;
+                            S.log_bead[li] = k;
+                            S.log_de[li] = v;
+                            S.log_theta[li] = theta;
+                            S.log_acc[li] = acc_i ? 1 : 0;
+                        }
                     }
                 }
-                __syncthreads();
-                // ---- the chain in shared memory, the log, the energy sum
-                if (tid == 0)
-                    for (unsigned m = amask; m; m &= m - 1) {
-                        const int l = __ffs(m) - 1;
-                        const int kl = __float_as_int(GP[l].w);
-                        P[kl] = GPN[l];
-                        MOV[kl] = 1;
-                    }
-                if (logging && lane == 0 && warp < nd) {
-                    const size_t li = lrow + m0 + g0 + warp;
-                    S.log_bead[li] = __float_as_int(GP[warp].w);
-                    S.log_de[li] = GV[warp];
-                    S.log_theta[li] = D1[g0 + warp].x;
-                    S.log_acc[li] = (amask >> warp) & 1u;
-                }
-                for (unsigned m = amask; m; m &= m - 1) {
-                    dsum = df_add(dsum, df{GV[__ffs(m) - 1], 0.f});
-                    ++nacc;
+                // With the log on, a rejected move's value may read the old position of a later
+                // group move; only then do the stores wait for every warp.
+                if (logging) __syncthreads();
+                if (warp < nd && lane == 0 && ((amask >> warp) & 1u)) {
+                    P[k] = make_float4(pn.x, pn.y, pn.z, 0.f);
+                    MOV[k] = 1;
                 }
                 __syncthreads();
                 g0 += nd;
             }
         }
-        // the deferred corrections of every warp, added in warp order
+        // every warp's accepted dE and deferred corrections, added in warp order
         if (npend > 0) cw = __fadd_rn(cw, pending_correction(PE, npend, lane));
         npend = 0;
-        if (lane == 0) CW[warp] = cw;
+        if (lane == 0) {
+            CW[4 * warp] = wdsum.hi;
+            CW[4 * warp + 1] = wdsum.lo;
+            CW[4 * warp + 2] = cw;
+            CW[4 * warp + 3] = __int_as_float(wnacc);
+        }
         cw = 0.f;
+        wdsum = df{0.f, 0.f};
+        wnacc = 0;
         __syncthreads();
-        for (int w2 = 0; w2 < W; ++w2) dsum = df_add(dsum, df{CW[w2], 0.f});
+        for (int w2 = 0; w2 < W; ++w2) {
+            dsum = df_add(dsum, df{CW[4 * w2], CW[4 * w2 + 1]});
+            dsum = df_add(dsum, df{CW[4 * w2 + 2], 0.f});
+            nacc += __float_as_int(CW[4 * w2 + 3]);
+        }
         E = (E + (double)dsum.hi) + (double)dsum.lo;
         if (warp == 0) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
     }
@@ -508,7 +523,7 @@ int grp_warps(int nmax) { return nmax <= 200 ? 4 : 8; }
 
 size_t grp_smem_bytes(int nmax, int warps) {
     const size_t fixed = warps == 4 ? grp_fixed_bytes<4>() : grp_fixed_bytes<8>();
-    return (size_t)nmax * sizeof(float4) + fixed + 4 * sizeof(float) * ((warps + 3) / 4) +
+    return (size_t)nmax * sizeof(float4) + fixed + 4 * sizeof(float) * warps +
            (size_t)warps * 3 * kPend * sizeof(float4) + (size_t)warps * nmax * sizeof(int) + (size_t)nmax + 16;
 }
 

@@ -520,15 +520,108 @@ def run_reweight(args):
     return 0
 
 
+def _oracle_rate(N, R, T, seed, sweeps, threads, xe=1, ens_id=0):
+    """Oracle single-bead updates/s of one ensemble (N, R) over `sweeps` sweeps."""
+    import oracle
+    from paper_1107_3490_gb300 import inputs
+    ens = oracle.OracleEnsemble(inputs.random_coil(N, R, seed, ens_id), T, seed, ensemble_id=ens_id,
+                                n_bins=1024, e_min=-8.0 * N, e_max=2.0 * N, threads=threads)
+    t0 = time.perf_counter()
+    ens.run(sweeps, xe)
+    return R * N * sweeps / (time.perf_counter() - t0)
+
+
+def _gpu_rate(specs, sweeps, warm=20):
+    """GPU single-bead updates/s and FP32 flops/s of one batched context over `sweeps` sweeps
+    (autotuned kernel, exchange every sweep)."""
+    from paper_1107_3490_gb300 import inputs, pt
+    made = [pt.make_params(N, inputs.temperature_ladder(tl, th, R), seed, ensemble_id=e,
+                           init_positions=inputs.random_coil(N, R, seed, e), n_bins=1024, recompute_every=1000)
+            for (N, R, tl, th, seed, e) in specs]
+    h = pt.pt_create_batch([p for p, _ in made])
+    pt.pt_sweep(h, warm, 1)
+    kern = pt.pt_autotune(h, max(4, min(100, sweeps // 4)), force=True)
+    pt.pt_sweep(h, 4, 1)
+    pt.pt_sync(h)
+    t0 = time.perf_counter()
+    pt.pt_sweep(h, sweeps, 1)
+    pt.pt_sync(h)
+    dt = time.perf_counter() - t0
+    pt.pt_destroy(h)
+    upd = sum(N * R for (N, R, *_) in specs) * sweeps
+    flops = sum(N * R * 30 * (N - 1) for (N, R, *_) in specs) * sweeps
+    return upd / dt, flops / dt, KERNEL_NAMES.get(kern, str(kern))
+
+
+def run_table(args):
+    """Oracle (all host cores and one core, bounded samples) and GPU single-bead updates/s for
+    the five configurations: plain N=30 x 16; N=100 x 64 x 4 ensembles; N=300 and N=1000 x 128;
+    256 uneven ensembles; the served job stream (run through the job server)."""
+    import numpy as np
+    from paper_1107_3490_gb300 import inputs
+    cores = os.cpu_count() or 1
+    peak = fp32_peak_tflops(152, 2070.0) * 1e12
+    rows = []
+
+    def add(name, gpu, flops, kern, orc_all, orc_1, sample, extra=None):
+        row = {"config": name, "gpu_updates_s": gpu, "fp32_peak_frac": flops / peak, "sweep_kernel": kern,
+               "oracle_updates_s_all_cores": orc_all, "oracle_updates_s_1core": orc_1, "oracle_sample": sample}
+        if extra:
+            row.update(extra)
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+
+    T30 = inputs.temperature_ladder(0.3, 3.0, 16)
+    g, f, k = _gpu_rate([(30, 16, 0.3, 3.0, 1, 0)], 1000)
+    add("1 plain N=30 x 16 replicas, T 0.3-3.0, 1000 sweeps", g, f, k,
+        _oracle_rate(30, 16, T30, 1, 1000, cores), _oracle_rate(30, 16, T30, 1, 300, 1), "full run / 300 sweeps")
+    T100 = inputs.temperature_ladder(0.2, 3.0, 64)
+    g, f, k = _gpu_rate([(100, 64, 0.2, 3.0, s, s - 1) for s in range(1, 5)], 1000)
+    add("2 N=100 x 64 replicas x 4 ensembles, T 0.2-3.0", g, f, k,
+        _oracle_rate(100, 64, T100, 1, 400, cores), _oracle_rate(100, 64, T100, 1, 30, 1),
+        "ensemble seed 1: 400 sweeps / 30 sweeps")
+    T128 = inputs.temperature_ladder(0.2, 3.0, 128)
+    for N, sw, so_all, so_1 in ((300, 200, 40, 3), (1000, 40, 4, 1)):
+        g, f, k = _gpu_rate([(N, 128, 0.2, 3.0, 1, 0)], sw)
+        add(f"3 N={N} x 128 replicas, T 0.2-3.0", g, f, k, _oracle_rate(N, 128, T128, 1, so_all, cores),
+            _oracle_rate(N, 128, T128, 1, so_1, 1), f"prefix: {so_all} sweeps / {so_1} sweeps")
+    specs = inputs.batched_ensembles(256)
+    g, f, k = _gpu_rate([(sp.n_beads, sp.n_replicas, 0.2, 3.0, sp.seed, sp.ensemble_id) for sp in specs], 100)
+    o_all = [_oracle_rate(sp.n_beads, sp.n_replicas, sp.temperatures(), sp.seed, 10, cores, ens_id=sp.ensemble_id)
+             for sp in specs[:8]]
+    o_one = [_oracle_rate(sp.n_beads, sp.n_replicas, sp.temperatures(), sp.seed, 3, 1, ens_id=sp.ensemble_id)
+             for sp in specs[:8]]
+    w = np.array([sp.n_beads * sp.n_replicas for sp in specs[:8]], dtype=float)
+    hm = lambda r: float(w.sum() / np.sum(w / np.array(r)))  # updates over time of the sample
+    add("4 batched 256 uneven ensembles (N 20-500, 8-64 replicas)", g, f, k, hm(o_all), hm(o_one),
+        "first 8 ensembles: 10 sweeps / 3 sweeps each")
+    jobs = inputs.served_jobs(4, s_lo=100, s_hi=1000)
+    o_all = [_oracle_rate(j.n_beads, j.n_replicas, j.temperatures(), j.seed, 5, cores, ens_id=j.ensemble_id) for j in jobs]
+    o_one = [_oracle_rate(j.n_beads, j.n_replicas, j.temperatures(), j.seed, 2, 1, ens_id=j.ensemble_id) for j in jobs]
+    w = np.array([j.n_beads * j.n_replicas for j in jobs], dtype=float)
+    rows.append({"config": "5 served job stream (oracle only; GPU: --workload served)",
+                 "oracle_updates_s_all_cores": float(w.sum() / np.sum(w / np.array(o_all))),
+                 "oracle_updates_s_1core": float(w.sum() / np.sum(w / np.array(o_one))),
+                 "oracle_sample": "first 4 jobs of the stream: 5 sweeps / 2 sweeps each"})
+    line = {"metric": "single-bead updates/s per configuration (GPU and FP64 oracle)", "unit": "updates/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "configurations 1-4; the served stream has its own workload (--workload served)",
+                       "host_cores": cores, "fp32_peak_tflops": peak / 1e12},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["plain", "batched", "served", "paper", "reweight"], default="plain",
+    ap.add_argument("--workload", choices=["plain", "batched", "served", "paper", "reweight", "table"], default="plain",
                     help="plain: the benchmark line; batched / served: the uneven-ensemble and job-stream forms; "
-                         "paper: the paper's S_p protocol; reweight: histogram reweighting time")
+                         "paper: the paper's S_p protocol; reweight: histogram reweighting time; "
+                         "table: GPU and oracle rates of the five configurations")
     ap.add_argument("--jobs", type=int, default=200)
     ap.add_argument("--rate", type=float, default=40.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -550,6 +643,8 @@ def main(argv=None):
         return run_paper(args)
     if args.workload == "reweight":
         return run_reweight(args)
+    if args.workload == "table":
+        return run_table(args)
     return run_gpu(args)
 
 

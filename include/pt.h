@@ -220,7 +220,7 @@ int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonde
 int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, double* out,
                            void* stream);
 
-/* Choose the sweep kernel (creation picks 0 below 24 beads, 4 up to 96, 5 up to 1024, else 3):
+/* Choose the sweep kernel (creation picks 0 below 24 beads, 4 up to 96, 5 up to 1024, else 2):
  * 0 = one warp per replica, one move at a time;
  * 1 = one warp per replica, groups of up to 8 consecutive moves with distinct beads
  * evaluated together; 2 = a CTA of 1-8 warps per replica (by N), one move at a time;
@@ -233,7 +233,9 @@ int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, 
  * summation order of dE. Kernels 4 and 5 take each Metropolis decision whose dE lies
  * outside its FP32 error bound of theta exactly, so they run that chain too except where a
  * dE falls within the parity tolerance of its threshold (and 4 and 5 run the same chain).
- * PT_EINVAL for an unknown kernel or kernel 4 or 5 with N_max > 1024. */
+ * PT_EINVAL for an unknown kernel, kernel 4 or 5 with N_max > 1024, or a kernel whose
+ * shared memory for N_max exceeds the GPU's per-block limit (kernel 3 above ~4500 beads);
+ * the context stays usable. */
 int pt_set_sweep_kernel(pt_ctx* h, int variant);
 
 /* The kernel in use (creation picks one from the chain length; see pt_autotune). */

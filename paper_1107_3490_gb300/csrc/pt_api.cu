@@ -49,7 +49,7 @@ int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 struct pt_ctx {
     std::vector<EnsHost> ens;
     std::vector<RepDev> reps;
-    int G = 0, P = 0, nmax = 0, warps = 1, num_sms = 152;
+    int G = 0, P = 0, nmax = 0, warps = 1, num_sms = 152, smem_optin = 227 * 1024;
     int variant = kSweepSimple;
     std::string gpu_name;
     int64_t H = 0;
@@ -80,6 +80,7 @@ constexpr int64_t kMaxChunk = 1000;
 
 int cuda_fail(pt_ctx* h, cudaError_t e, const char* what) {
     if (h) h->poisoned = PT_ECUDA;
+    cudaGetLastError();  // a non-sticky error must not resurface at a later, unrelated check
     return fail(PT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -266,7 +267,7 @@ void drop_graph(pt_ctx* h) {
 // 128 replicas above): one warp per replica wins for short chains, the warp-per-move
 // lookahead from about 50 beads on.
 int default_variant(int nmax) {
-    return nmax < 24 ? kSweepSimple : nmax <= 96 ? kSweepReg : nmax <= kRegMaxN ? kSweepGrp : kSweepWpm;
+    return nmax < 24 ? kSweepSimple : nmax <= 96 ? kSweepReg : nmax <= kRegMaxN ? kSweepGrp : kSweepTeam;
 }
 
 pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
@@ -315,6 +316,7 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (ce != cudaSuccess) {
         fail(PT_ECUDA, "no usable CUDA device: %s", cudaGetErrorString(ce));
         delete h;
@@ -437,6 +439,7 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     h->warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, h->variant);
     ce = configure_sweep(h->nmax, h->warps, h->variant);
     if (ce != cudaSuccess) {
+        cudaGetLastError();
         fail(PT_ECUDA, "configure sweep kernel: %s", cudaGetErrorString(ce));
         pt_destroy(h);
         return nullptr;
@@ -631,6 +634,10 @@ extern "C" int pt_set_sweep_kernel(pt_ctx* h, int variant) {
         return fail(PT_EINVAL, "sweep kernel %d holds chains of at most %d beads", variant, kRegMaxN);
     if ((rc = sync_and_check(h))) return rc;
     const int warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, variant);
+    const size_t smem = sweep_smem_bytes(h->nmax, warps, variant);
+    if (smem > (size_t)h->smem_optin)
+        return fail(PT_EINVAL, "sweep kernel %d needs %zu bytes of shared memory per block for N=%d (the GPU has %d)",
+                    variant, smem, h->nmax, h->smem_optin);
     CK(h, configure_sweep(h->nmax, warps, variant));
     h->variant = variant;
     h->warps = warps;
@@ -695,6 +702,8 @@ extern "C" int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen) 
     const int variants[] = {kSweepSimple, kSweepLookahead, kSweepTeam, kSweepWpm, kSweepReg, kSweepGrp};
     for (int v : variants) {
         if ((v == kSweepReg || v == kSweepGrp) && h->nmax > kRegMaxN) continue;
+        if (sweep_smem_bytes(h->nmax, sweep_warps_per_block(h->nmax, h->G, h->num_sms, v), v) > (size_t)h->smem_optin)
+            continue;
         if ((rc = pt_set_sweep_kernel(h, v))) break;
         if ((rc = pt_sweep(h, 2, 1))) break;  // warm-up (and graph capture)
         CK(h, cudaEventRecord(a, h->stream));

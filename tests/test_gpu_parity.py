@@ -195,3 +195,82 @@ def test_kernels_agree_on_a_hot_dense_case():
         assert np.array_equal(fin, np.isfinite(b["de"]))
         d = np.abs(a["de"][fin].astype(np.float64) - b["de"][fin])
         assert np.all(d <= 2e-6 + 2e-5 * np.abs(a["de"][fin]))
+
+
+@pytest.mark.parametrize("variant", [4, 5])
+def test_benchmark_configuration_sampled(variant):
+    """The benchmark's workload in its launch configuration: four ensembles (seeds 1-4) of
+    N = 100 x 64 replicas, T 0.2-3.0, 4096 bins, in one batched context; ensembles 0 and 3
+    move for move against the oracle over the first 10 sweeps."""
+    S, N, R = 10, 100, 64
+    T = inputs.temperature_ladder(0.2, 3.0, R)
+    made = [pt.make_params(N, T, e + 1, ensemble_id=e, init_positions=inputs.random_coil(N, R, e + 1, e),
+                           n_bins=4096, recompute_every=1000) for e in range(4)]
+    h = pt.pt_create_batch([p for p, _ in made])
+    try:
+        pt.pt_set_sweep_kernel(h, variant)
+        pt.pt_set_debug_log(h, 0, S)
+        pt.pt_sweep(h, S, 1)
+        g = pt.pt_get_debug_log(h, S)
+        pos = pt.pt_get_positions(h).reshape(4, R, N, 3)
+    finally:
+        pt.pt_destroy(h)
+    for e in (0, 3):
+        orc = oracle.OracleEnsemble(inputs.random_coil(N, R, e + 1, e), T, e + 1, ensemble_id=e, n_bins=4096,
+                                    recompute_every=1000, threads=16)
+        o = parity.oracle_log_with_labels(orc, S, 1)
+        rep = parity.compare(g, o, R, N, T, e + 1, e, rep_offset=R * e, pos_offset=R * N * e, n_reps_total=4 * R)
+        assert rep.ok, (e, rep.failures)
+        assert rep.moves_compared > R * N
+        if rep.divergence is None:
+            assert np.array_equal(pos[e], orc.pos)
+
+
+@pytest.mark.parametrize("N,S", [(300, 2), (1000, 1)])
+def test_long_chains_at_128_replicas(N, S):
+    """The long-chain configurations at their replica count (128), first sweeps, with the
+    kernel the library picks for them."""
+    R = 128
+    T = inputs.temperature_ladder(0.2, 3.0, R)
+    rep, out, orc = _run(N, R, S, seed=1, tmin=0.2, variant=pt_default_kernel(N))
+    assert rep.ok, rep.failures
+    assert rep.moves_compared > 0
+
+
+def pt_default_kernel(N):
+    h = pt.pt_create(N, 2, np.array([1.0, 2.0]), 1)
+    try:
+        return pt.pt_get_sweep_kernel(h)
+    finally:
+        pt.pt_destroy(h)
+
+
+@pytest.mark.parametrize("variant", [0, 2, 3])
+@pytest.mark.parametrize("N", [2048, 8192])
+def test_longest_chains(N, variant):
+    """Chains beyond the register kernels' 1024 beads, up to the largest N the library takes
+    (the warp-per-move kernel's shared memory does not fit 8192 beads: a clean PT_EINVAL)."""
+    if variant == 3 and N == 8192:
+        h = pt.pt_create(N, 2, np.array([1.0, 2.0]), 1)
+        try:
+            with pytest.raises(pt.PtError):
+                pt.pt_set_sweep_kernel(h, 3)
+            pt.pt_sweep(h, 1, 1)  # still usable with its own kernel
+        finally:
+            pt.pt_destroy(h)
+        return
+    rep, out, orc = _run(N, 2 if N < 8192 else 1, 1, seed=2, tmin=0.2, variant=variant)
+    assert rep.ok, rep.failures
+    assert rep.moves_compared > 0
+
+
+def test_register_kernels_reject_longer_chains():
+    h = pt.pt_create(1025, 2, np.array([1.0, 2.0]), 1)
+    try:
+        for v in (4, 5):
+            with pytest.raises(pt.PtError):
+                pt.pt_set_sweep_kernel(h, v)
+        pt.pt_sweep(h, 0, 1)  # zero sweeps: nothing to do, no error
+        assert pt.pt_counters(h, 0)[0] == 0
+    finally:
+        pt.pt_destroy(h)

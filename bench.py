@@ -33,10 +33,10 @@ METRIC = "single-bead Metropolis updates/sec (all replicas)"
 KERNEL_NAMES = {0: "k_sweep", 1: "k_sweep_la", 2: "k_sweep_team", 3: "k_sweep_wpm", 4: "k_sweep_reg",
                 5: "k_sweep_grp"}
 UNIT = "updates/s"
-# DRAM bytes read + written per sweep launch on this workload (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum, one capture of the kernel as it stands); kernels without a current
-# capture report null
-TRAFFIC_BYTES = {"k_sweep_grp": 648704, "k_sweep_reg": 637184}
+# DRAM bytes read + written per sweep on this workload (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch of the kernel as it stands, divided by the sweeps that
+# launch ran), keyed by (kernel, launch mode); pairs without a current capture report null
+TRAFFIC_BYTES = {("k_sweep_grp", 1): 2264, ("k_sweep_reg", 1): 2187}
 WORKLOAD = (f"PT polymer N={N_BEADS} beads, {N_REP} replicas at T geometric {T_MIN}-{T_MAX}, "
             f"{N_ENS} ensembles (seeds 1-{N_ENS}) per GPU, delta 0.3, exchange every sweep, "
             f"FP64 recompute every 1000 sweeps, 4096 FP64 bins/slot; 1 step = {SWEEPS_PER_STEP} sweeps")
@@ -244,6 +244,7 @@ def run_gpu(args):
             dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     kernel_ms, kernel_n = pt.pt_kernel_timing(h)
+    lmode = pt.pt_get_launch_mode(h)
     pt.pt_sync(h)
     local_ms = sum(step_ms)
     total_ms = reduce_max(local_ms, dist, dev)
@@ -272,14 +273,18 @@ def run_gpu(args):
     achieved = pairs_per_launch * FLOPS_PER_PAIR / (kernel_ms / 1e3) / 1e12
     peak = fp32_peak_tflops(num_sms, 2070.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_BYTES.get(KERNEL_NAMES[kernel]), "kernel": KERNEL_NAMES[kernel],
-                "launch_ms": kernel_ms, "launches_sampled": kernel_n,
+                "traffic": TRAFFIC_BYTES.get((KERNEL_NAMES[kernel], lmode)), "traffic_unit": "bytes per sweep",
+                "kernel": KERNEL_NAMES[kernel],
+                "kernel_ms_per_sweep": kernel_ms, "launches_sampled": kernel_n,
+                "launch_mode": "persistent (exchange in kernel)" if lmode == 1 else "graph per sweep",
                 "peak_basis": f"{num_sms} SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)"}
     if clocks and clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / fp32_peak_tflops(num_sms, clocks["sm_mhz"])
     pt.pt_destroy(h)
 
-    launches_per_step = 1 + -(-SWEEPS_PER_STEP // 32) * 64
+    # every step: the target-setting launch, then one cooperative launch (persistent mode)
+    # or graphs of 32 (sweep, exchange) launch pairs
+    launches_per_step = 2 if lmode == 1 else 1 + -(-SWEEPS_PER_STEP // 32) * 64
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

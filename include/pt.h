@@ -241,17 +241,30 @@ int pt_set_sweep_kernel(pt_ctx* h, int variant);
 /* The kernel in use (creation picks one from the chain length; see pt_autotune). */
 int pt_get_sweep_kernel(const pt_ctx* h);
 
-/* Autotuner: time every sweep kernel on this context for trial_sweeps sweeps (exchange
- * every sweep) and keep the fastest. The state is checkpointed before and restored after,
+/* Autotuner: time every sweep kernel (kernels 4 and 5 in both launch modes, see
+ * pt_set_launch_mode) on this context for trial_sweeps sweeps (exchange every sweep) and
+ * keep the fastest kernel and mode. The state is checkpointed before and restored after,
  * so the chain does not advance. The choice is cached per (GPU name, largest N, replica
  * count) in the process and, when the environment variable PTGB_AUTOTUNE_CACHE names a
  * file, in that file; force = 1 measures again. *chosen (may be NULL) gets the kernel. */
 int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen);
 
+/* Launch mode. 1 (default): with kernel 4 or 5, when every replica's block can be resident
+ * at once, a pt_sweep call with exchange_every >= 1 is one cooperative launch that runs all
+ * its sweeps, each ensemble's exchange rounds done inside the kernel: the replicas of an
+ * ensemble meet at a device barrier after the sweep an exchange follows, the ensemble's
+ * first replica runs the round (Eq. 6) and releases the others. Every wait is bounded (about
+ * a second); a wait that gives up makes the call's later checks return PT_ETIMEOUT. 0: one
+ * launch per sweep (replayed from a CUDA graph) and a separate exchange kernel. Both modes
+ * run the same chain. pt_get_launch_mode returns the mode pt_sweep will actually use. */
+int pt_set_launch_mode(pt_ctx* h, int mode);
+int pt_get_launch_mode(const pt_ctx* h);
+
 /* Kernel timing for profiling: with on = 1 every sweep-kernel launch is bracketed by CUDA
  * events on the context's stream (inside the captured graph too). pt_kernel_timing then
- * reports the mean duration of the sweep launches that did work in the most recent graph
- * replay (or of the last <= 64 direct launches) and how many launches that mean covers. */
+ * reports the mean sweep-kernel time per sweep over the launches that did work in the most
+ * recent graph replay (or the last <= 64 direct or persistent launches) and how many
+ * launches that mean covers. */
 int pt_set_kernel_timing(pt_ctx* h, int on);
 int pt_kernel_timing(pt_ctx* h, double* mean_sweep_ms, int* n_launches);
 

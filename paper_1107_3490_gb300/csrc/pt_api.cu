@@ -68,8 +68,13 @@ struct pt_ctx {
     int64_t log_s0 = 0, log_ns = 0;
     // optional per-launch timing of the sweep kernel: event pairs, ring of kTimingSlots
     std::vector<cudaEvent_t> tev;
+    std::vector<int64_t> t_sweeps;  // sweeps of each timed launch
     int t_next = 0, t_count = 0;
     bool t_graph = false;  // the recorded pairs come from the last graph replay
+    // launch mode: 1 = one persistent cooperative launch per call with the exchange inside
+    // the kernel (kernels 4 and 5, when the grid fits at once); 0 = per-sweep launches
+    int launch_mode = 1;
+    bool coop_ok = false;  // the current kernel's grid can be resident at once
 };
 
 namespace {
@@ -77,6 +82,7 @@ namespace {
 constexpr int kGraphSweeps = 32;
 constexpr int kTimingSlots = 64;
 constexpr int64_t kMaxChunk = 1000;
+constexpr int64_t kMaxPersistent = 1 << 20;  // sweeps per persistent launch
 
 int cuda_fail(pt_ctx* h, cudaError_t e, const char* what) {
     if (h) h->poisoned = PT_ECUDA;
@@ -190,7 +196,7 @@ void free_state(pt_ctx* h) {
     State& S = h->S;
     void* ptrs[] = {S.reps, S.ens, S.pos, S.E, S.temp_of_rep, S.rep_of_temp, S.Tf, S.beta, S.hist,
                     S.outl, S.mom, S.obs, S.obs_rg2_hist, S.obs_ree2_hist, S.mv_att, S.mv_acc, S.ex_att,
-                    S.ex_acc, S.drift, S.rep_sweep, S.err, S.log_bead, S.log_de, S.log_theta, S.log_acc,
+                    S.ex_acc, S.drift, S.rep_sweep, S.err, S.xarrive, S.xdone, S.log_bead, S.log_de, S.log_theta, S.log_acc,
                     S.log_e, S.log_x, h->scratch, h->conf_buf, h->eout_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -246,13 +252,25 @@ int upload_positions(pt_ctx* h, const std::vector<float>& xyz) {
 }
 
 // Sweep launch, bracketed by a timing event pair when timing is on.
-cudaError_t timed_sweep(pt_ctx* h, int chunk) {
-    if (h->tev.empty()) return launch_sweep(h->S, chunk, h->warps, h->variant, h->stream);
+// One sweep-kernel launch of up to `chunk` sweeps (persistent: the cooperative kernel with
+// the exchange inside), bracketed by timing events when timing is on.
+cudaError_t timed_sweep(pt_ctx* h, int chunk, bool persistent = false) {
+    auto go = [&]() {
+        return persistent ? launch_sweep_coop(h->S, chunk, h->variant, h->stream)
+                          : launch_sweep(h->S, chunk, h->warps, h->variant, h->stream);
+    };
+    if (h->tev.empty()) return go();
     const int i = h->t_next;
-    // External records stay visible to the host when captured into a graph.
-    cudaError_t e = cudaEventRecordWithFlags(h->tev[2 * i], h->stream, cudaEventRecordExternal);
-    if (e == cudaSuccess) e = launch_sweep(h->S, chunk, h->warps, h->variant, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecordWithFlags(h->tev[2 * i + 1], h->stream, cudaEventRecordExternal);
+    // External records stay visible to the host when captured into a graph; outside a
+    // capture the flag is refused, so plain records there.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(h->stream, &cs);
+    if (e != cudaSuccess) return e;
+    const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    e = cudaEventRecordWithFlags(h->tev[2 * i], h->stream, flags);
+    if (e == cudaSuccess) e = go();
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(h->tev[2 * i + 1], h->stream, flags);
+    h->t_sweeps[i] = chunk;
     h->t_next = (i + 1) % kTimingSlots;
     h->t_count = std::min(h->t_count + 1, kTimingSlots);
     return e;
@@ -361,6 +379,8 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     A(dalloc(&S.drift, G));
     A(dalloc(&S.rep_sweep, G));
     A(dalloc(&S.err, 1));
+    A(dalloc(&S.xarrive, (size_t)n_ens));
+    A(dalloc(&S.xdone, (size_t)n_ens));
     if (a != cudaSuccess) {
         fail(a == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA, "device allocation: %s", cudaGetErrorString(a));
         pt_destroy(h);
@@ -444,6 +464,7 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
         pt_destroy(h);
         return nullptr;
     }
+    h->coop_ok = sweep_coop_fits(h->S, h->nmax, h->variant, h->num_sms);
     return h;
 }
 
@@ -595,7 +616,17 @@ extern "C" int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every) {
                                                                                exchange_every);
     CK(h, cudaGetLastError());
     const int xe = exchange_every;
-    if (xe == 1) {
+    if (xe >= 1 && h->launch_mode == 1 && h->coop_ok) {
+        // persistent: each launch runs every ensemble up to its target (or chunk sweeps),
+        // exchange rounds inside the kernel
+        if (h->t_graph) {
+            h->t_graph = false;
+            h->t_count = 0;
+            h->t_next = 0;
+        }
+        for (int64_t left = n_sweeps; left > 0; left -= kMaxPersistent)
+            CK(h, timed_sweep(h, (int)std::min<int64_t>(left, kMaxPersistent), true));
+    } else if (xe == 1) {
         if (!h->graph1 && (rc = build_graph1(h))) return rc;
         // repeated launches past the target do nothing: sweeps stop at the target and the
         // exchange kernel runs once per completed sweep
@@ -641,8 +672,23 @@ extern "C" int pt_set_sweep_kernel(pt_ctx* h, int variant) {
     CK(h, configure_sweep(h->nmax, warps, variant));
     h->variant = variant;
     h->warps = warps;
+    h->coop_ok = sweep_coop_fits(h->S, h->nmax, variant, h->num_sms);
     drop_graph(h);
     return PT_OK;
+}
+
+extern "C" int pt_set_launch_mode(pt_ctx* h, int mode) {
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (mode != 0 && mode != 1) return fail(PT_EINVAL, "launch mode must be 0 or 1");
+    if ((rc = sync_and_check(h))) return rc;
+    h->launch_mode = mode;
+    return PT_OK;
+}
+
+extern "C" int pt_get_launch_mode(const pt_ctx* h) {
+    if (!h) return -1;
+    return (h->launch_mode == 1 && h->coop_ok && (h->variant == kSweepReg || h->variant == kSweepGrp)) ? 1 : 0;
 }
 
 namespace {
@@ -685,8 +731,10 @@ extern "C" int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen) 
         tune_load();
         auto it = g_tune.find(key);
         if (!force && it != g_tune.end()) {
-            if ((rc = pt_set_sweep_kernel(h, it->second))) return rc;
-            if (chosen) *chosen = it->second;
+            // cached as kernel + 256 x launch mode
+            if ((rc = pt_set_sweep_kernel(h, it->second & 0xff))) return rc;
+            h->launch_mode = it->second >> 8;
+            if (chosen) *chosen = it->second & 0xff;
             return PT_OK;
         }
     }
@@ -697,7 +745,7 @@ extern "C" int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen) 
     cudaEvent_t a = nullptr, b = nullptr;
     CK(h, cudaEventCreate(&a));
     CK(h, cudaEventCreate(&b));
-    int best = h->variant;
+    int best = h->variant, best_mode = h->launch_mode;
     float best_ms = 1e30f;
     const int variants[] = {kSweepSimple, kSweepLookahead, kSweepTeam, kSweepWpm, kSweepReg, kSweepGrp};
     for (int v : variants) {
@@ -705,28 +753,36 @@ extern "C" int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen) 
         if (sweep_smem_bytes(h->nmax, sweep_warps_per_block(h->nmax, h->G, h->num_sms, v), v) > (size_t)h->smem_optin)
             continue;
         if ((rc = pt_set_sweep_kernel(h, v))) break;
-        if ((rc = pt_sweep(h, 2, 1))) break;  // warm-up (and graph capture)
-        CK(h, cudaEventRecord(a, h->stream));
-        if ((rc = pt_sweep(h, trial_sweeps, 1))) break;
-        CK(h, cudaEventRecord(b, h->stream));
-        if ((rc = sync_and_check(h))) break;
-        float ms = 0.f;
-        CK(h, cudaEventElapsedTime(&ms, a, b));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = v;
+        // kernels 4 and 5 also in both launch modes (persistent where the grid fits)
+        for (int mode = 1; mode >= 0; --mode) {
+            if (mode == 1 && !(h->coop_ok && (v == kSweepReg || v == kSweepGrp))) continue;
+            h->launch_mode = mode;
+            if ((rc = pt_sweep(h, 2, 1))) break;  // warm-up (and graph capture)
+            CK(h, cudaEventRecord(a, h->stream));
+            if ((rc = pt_sweep(h, trial_sweeps, 1))) break;
+            CK(h, cudaEventRecord(b, h->stream));
+            if ((rc = sync_and_check(h))) break;
+            float ms = 0.f;
+            CK(h, cudaEventElapsedTime(&ms, a, b));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = v;
+                best_mode = mode;
+            }
+            if ((rc = pt_restore(h, snap.data(), snap.size()))) break;
         }
-        if ((rc = pt_restore(h, snap.data(), snap.size()))) break;
+        if (rc) break;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (rc) return rc;
     if ((rc = pt_set_sweep_kernel(h, best))) return rc;
+    h->launch_mode = best_mode;
     if ((rc = pt_restore(h, snap.data(), snap.size()))) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[key] = best;
-        tune_store(h->gpu_name, h->nmax, h->G, best);
+        g_tune[key] = best | (best_mode << 8);
+        tune_store(h->gpu_name, h->nmax, h->G, best | (best_mode << 8));
     }
     if (chosen) *chosen = best;
     return PT_OK;
@@ -745,6 +801,7 @@ extern "C" int pt_set_kernel_timing(pt_ctx* h, int on) {
     drop_graph(h);
     if (on) {
         h->tev.resize(2 * kTimingSlots);
+        h->t_sweeps.assign(kTimingSlots, 1);
         for (auto& ev : h->tev) CK(h, cudaEventCreate(&ev));
     }
     return PT_OK;
@@ -756,13 +813,15 @@ extern "C" int pt_kernel_timing(pt_ctx* h, double* mean_sweep_ms, int* n_launche
     if (h->tev.empty()) return fail(PT_EINVAL, "kernel timing is off");
     if ((rc = sync_and_check(h))) return rc;
     double sum = 0.0;
+    int64_t sweeps = 0;
     const int n = h->t_count;
     for (int i = 0; i < n; ++i) {
         float ms = 0.f;
         CK(h, cudaEventElapsedTime(&ms, h->tev[2 * i], h->tev[2 * i + 1]));
         sum += ms;
+        sweeps += h->t_graph ? 1 : h->t_sweeps[i];
     }
-    if (mean_sweep_ms) *mean_sweep_ms = n ? sum / n : 0.0;
+    if (mean_sweep_ms) *mean_sweep_ms = sweeps ? sum / (double)sweeps : 0.0;
     if (n_launches) *n_launches = n;
     return PT_OK;
 }
@@ -1043,10 +1102,20 @@ extern "C" int pt_restore(pt_ctx* h, const void* buf, size_t size) {
         return fail(PT_EINVAL, "pt_restore: checkpoint belongs to a context of another shape or parameters");
     if ((rc = sync_and_check(h))) return rc;
     const char* p = (const char*)buf + sizeof hdr;
+    std::vector<EnsDev> eds(h->ens.size());
     for (auto& b : bl) {
+        if (b.dev == (void*)h->S.ens) std::memcpy(eds.data(), p, b.bytes);
         CK(h, cudaMemcpy(b.dev, p, b.bytes, cudaMemcpyHostToDevice));
         p += b.bytes;
     }
+    // the in-kernel exchange barrier counts R arrivals and one release per round
+    std::vector<unsigned long long> arr(eds.size()), rel(eds.size());
+    for (size_t e = 0; e < eds.size(); ++e) {
+        rel[e] = (unsigned long long)eds[e].xround;
+        arr[e] = rel[e] * (unsigned long long)eds[e].R;
+    }
+    CK(h, cudaMemcpy(h->S.xarrive, arr.data(), arr.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->S.xdone, rel.data(), rel.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
     h->done = (int64_t)hdr[2];
     return PT_OK;
 }

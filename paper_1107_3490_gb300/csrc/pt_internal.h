@@ -54,6 +54,11 @@ struct State {
     double* drift;            // [replica]
     int64_t* rep_sweep;       // [replica] sweeps done
     int* err;                 // error bits
+    // in-kernel exchange of persistent launches: per ensemble, arrivals at the ensemble
+    // barrier (R per round) and rounds released; xin != 0 in such a launch
+    unsigned long long* xarrive;
+    unsigned long long* xdone;
+    int xin;
     // per-move log of sweeps [log_s0, log_s0 + log_ns); null pointers when off
     int64_t log_s0, log_ns, log_pstride;  // log_pstride = total positions
     int32_t* log_bead;
@@ -78,15 +83,24 @@ constexpr int kRegMaxN = 1024;
 int reg_slots(int nmax);
 size_t reg_smem_bytes(int nmax);
 cudaError_t launch_sweep_reg(const State& s, int chunk, cudaStream_t st);
+bool reg_coop_fits(const State& s, int nmax, int num_sms);
+cudaError_t launch_sweep_reg_coop(const State& s, int chunk, cudaStream_t st);
 int grp_warps(int nmax);
 size_t grp_smem_bytes(int nmax, int warps);
 cudaError_t configure_sweep_grp(int nmax);
 cudaError_t launch_sweep_grp(const State& s, int chunk, cudaStream_t st);
+bool grp_coop_fits(const State& s, int nmax, int num_sms);
+cudaError_t launch_sweep_grp_coop(const State& s, int chunk, cudaStream_t st);
 int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant);
 size_t sweep_smem_bytes(int nmax, int warps, int variant);
 cudaError_t configure_sweep(int nmax, int warps, int variant);  // per context, before any capture
 cudaError_t launch_sweep(const State& s, int chunk, int warps, int variant, cudaStream_t st);
 cudaError_t launch_exchange(const State& s, cudaStream_t st);
+// Persistent launches (kernels 4 and 5): all sweeps up to each ensemble's target in one
+// cooperative launch, exchange rounds inside the kernel. coop_fits: whether the whole grid
+// can be resident at once (the condition of a cooperative launch).
+bool sweep_coop_fits(const State& s, int nmax, int variant, int num_sms);
+cudaError_t launch_sweep_coop(const State& s, int chunk, int variant, cudaStream_t st);
 
 // FP64 total energy (Eq. 4) of n_conf conformations. Conformation c has N_c beads at
 // pos[off_c ...]; with reps == nullptr every conformation has N beads at pos[c * N].

@@ -848,47 +848,21 @@ __global__ void __launch_bounds__(NW * 32) k_sweep_wpm(State S, int chunk) {
     }
 }
 
-// One exchange round per ensemble that is due (Sec. 3.3, Eq. 6). One warp per ensemble;
-// the pairs of a round are disjoint, so lanes swap labels without conflicts.
+// One exchange round per ensemble that is due (Sec. 3.3, Eq. 6): one warp per ensemble. It
+// also keeps the in-kernel barrier's counters at R arrivals and one release per round.
 __global__ void k_exchange(State S) {
     const int lane = threadIdx.x & 31;
     const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (e >= S.n_ens) return;
-    EnsDev* ed = S.ens + e;
+    const EnsDev* ed = S.ens + e;
     const int base = ed->rep_base, R = ed->R;
     const int64_t sw = S.rep_sweep[base];
     const int xe = ed->exchange_every;
     if (xe <= 0 || R < 2 || sw == 0 || sw % xe != 0 || sw <= ed->last_x_sweep) return;
-    const int64_t x = ed->xround;
-    const int q = (int)(x & 1);
-    const uint32_t k0 = (uint32_t)ed->seed, k1 = (uint32_t)(ed->seed >> 32);
-    const int64_t s_log = sw - 1;
-    int8_t* xo = (S.log_x && s_log >= S.log_s0 && s_log < S.log_s0 + S.log_ns)
-                     ? S.log_x + (size_t)(s_log - S.log_s0) * S.n_reps + base
-                     : nullptr;
-    if (xo)
-        for (int t = lane; t < R; t += 32) xo[t] = -1;
-    __syncwarp();
-    for (int t = q + 2 * lane; t + 1 < R; t += 64) {
-        const int ra = S.rep_of_temp[base + t], rb = S.rep_of_temp[base + t + 1];
-        const double arg = (S.E[base + ra] - S.E[base + rb]) * (S.beta[base + t] - S.beta[base + t + 1]);
-        const u4 w = philox(u4{(uint32_t)t, (uint32_t)x, 0u, ed->ens_id | (kTagExch << 24)}, k0, k1);
-        const double u = (double)(w.x >> 8) * (1.0 / 16777216.0);
-        const bool acc = u < exp(arg);
-        S.ex_att[base + t] += 1ull;
-        if (acc) {
-            S.ex_acc[base + t] += 1ull;
-            S.rep_of_temp[base + t] = rb;
-            S.rep_of_temp[base + t + 1] = ra;
-            S.temp_of_rep[base + rb] = t;
-            S.temp_of_rep[base + ra] = t + 1;
-        }
-        if (xo) xo[t] = acc ? 1 : 0;
-    }
-    __syncwarp();
-    if (lane == 0) {
-        ed->xround = x + 1;
-        ed->last_x_sweep = sw;
+    exchange_round_warp(S, e, sw, lane);
+    if (lane == 0 && S.xarrive) {
+        S.xarrive[e] += (unsigned long long)R;
+        S.xdone[e] += 1ull;
     }
 }
 
@@ -1027,6 +1001,19 @@ cudaError_t launch_sweep(const State& s, int chunk, int warps, int variant, cuda
     else
         k_sweep<<<blocks, 32 * warps, smem, st>>>(s, chunk);
     return cudaGetLastError();
+}
+
+bool sweep_coop_fits(const State& s, int nmax, int variant, int num_sms) {
+    if (nmax > kRegMaxN) return false;
+    if (variant == kSweepReg) return reg_coop_fits(s, nmax, num_sms);
+    if (variant == kSweepGrp) return grp_coop_fits(s, nmax, num_sms);
+    return false;
+}
+
+cudaError_t launch_sweep_coop(const State& s, int chunk, int variant, cudaStream_t st) {
+    if (variant == kSweepReg) return launch_sweep_reg_coop(s, chunk, st);
+    if (variant == kSweepGrp) return launch_sweep_grp_coop(s, chunk, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_exchange(const State& s, cudaStream_t st) {

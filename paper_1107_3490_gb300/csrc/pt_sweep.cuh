@@ -68,6 +68,91 @@ __device__ __forceinline__ void warp_shape(const float4* P, int N, int lane, dou
     ree2 = ex * ex + ey * ey + ez * ez;
 }
 
+// One exchange round of ensemble e (Sec. 3.3, Eq. 6) by one warp: the pairs (t, t+1) of the
+// round's parity on different lanes (disjoint, so labels swap without conflicts). sw is the
+// ensemble's sweep count after the sweep the round follows. Accept iff u < exp(arg) in FP64.
+__device__ __forceinline__ void exchange_round_warp(const State& S, int e, int64_t sw, int lane) {
+    // reads of what other blocks of a persistent launch wrote bypass L1 (__ldcg)
+    EnsDev* ed = S.ens + e;
+    const int base = ed->rep_base, R = ed->R;
+    const int64_t x = __ldcg(&ed->xround);
+    const int q = (int)(x & 1);
+    const uint32_t k0 = (uint32_t)ed->seed, k1 = (uint32_t)(ed->seed >> 32);
+    const int64_t s_log = sw - 1;
+    int8_t* xo = (S.log_x && s_log >= S.log_s0 && s_log < S.log_s0 + S.log_ns)
+                     ? S.log_x + (size_t)(s_log - S.log_s0) * S.n_reps + base
+                     : nullptr;
+    if (xo)
+        for (int t = lane; t < R; t += 32) xo[t] = -1;
+    __syncwarp();
+    for (int t = q + 2 * lane; t + 1 < R; t += 64) {
+        const int ra = __ldcg(&S.rep_of_temp[base + t]), rb = __ldcg(&S.rep_of_temp[base + t + 1]);
+        const double arg = (__ldcg(&S.E[base + ra]) - __ldcg(&S.E[base + rb])) * (S.beta[base + t] - S.beta[base + t + 1]);
+        const u4 w = philox(u4{(uint32_t)t, (uint32_t)x, 0u, ed->ens_id | (kTagExch << 24)}, k0, k1);
+        const double u = (double)(w.x >> 8) * (1.0 / 16777216.0);
+        const bool acc = u < exp(arg);
+        S.ex_att[base + t] += 1ull;
+        if (acc) {
+            S.ex_acc[base + t] += 1ull;
+            S.rep_of_temp[base + t] = rb;
+            S.rep_of_temp[base + t + 1] = ra;
+            S.temp_of_rep[base + rb] = t;
+            S.temp_of_rep[base + ra] = t + 1;
+        }
+        if (xo) xo[t] = acc ? 1 : 0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        ed->xround = x + 1;
+        ed->last_x_sweep = sw;
+    }
+}
+
+// Bounded wait (lane 0 polls, the warp waits) until *p >= target; false if it gave up. A
+// poll costs at least 100 ns, so the limit is about a second or more, far above one sweep.
+constexpr long long kWaitPolls = 1ll << 23;
+__device__ __forceinline__ bool wait_at_least(unsigned long long* p, unsigned long long target, int lane) {
+    int ok = 1;
+    if (lane == 0) {
+        long long it = 0;
+        while (*(volatile unsigned long long*)p < target) {
+            if (++it > kWaitPolls) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// In-kernel exchange after sweep count sw, called by one warp of every replica of ensemble e
+// once that replica's energy S.E[g] is stored: the replica arrives at the ensemble barrier;
+// the ensemble's first replica waits for all R arrivals, runs the round and releases it;
+// the others wait for the release. xr counts the ensemble's rounds (the same in every
+// replica). False if a wait gave up.
+__device__ __forceinline__ bool ensemble_exchange(const State& S, int e, int g, int rep_base, int R, int64_t sw,
+                                                  int64_t& xr, int lane) {
+    if (lane == 0) {
+        __threadfence();
+        atomicAdd(&S.xarrive[e], 1ull);
+    }
+    bool ok;
+    if (g == rep_base) {
+        ok = wait_at_least(&S.xarrive[e], (unsigned long long)R * (unsigned long long)(xr + 1), lane);
+        if (ok) {
+            exchange_round_warp(S, e, sw, lane);
+            __threadfence();
+            if (lane == 0) atomicExch(&S.xdone[e], (unsigned long long)(xr + 1));
+        }
+    } else {
+        ok = wait_at_least(&S.xdone[e], (unsigned long long)(xr + 1), lane);
+    }
+    ++xr;
+    return ok;
+}
+
 // End of one sweep of replica g (all lanes of its warp call it): the periodic FP64
 // recompute of Eq. 4, then the measurement into the replica's temperature slot (the
 // replica owns the slot until the next exchange, so plain read-modify-write is race-free)

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
     const EnsDev ed = S.ens[rd.ens];
     const int N = rd.N;
     int64_t s = S.rep_sweep[g];
-    const int64_t s_end = min(ed.target, s + (int64_t)chunk);
+    int64_t s_end = min(ed.target, s + (int64_t)chunk);
     if (s >= s_end) return;  // uniform over the CTA
 
     float4* P = smem;                         // [nmax] chain at the start of the current group
@@ -129,9 +129,10 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
     }
 
     double E = S.E[g];
-    const int slot = S.temp_of_rep[g];
-    const int gs = rd.slot_base + slot;
-    const float Tf = S.Tf[gs];
+    int slot = S.temp_of_rep[g];
+    int gs = rd.slot_base + slot;
+    float Tf = S.Tf[gs];
+    int64_t xr = S.xin ? S.ens[rd.ens].xround : 0;  // exchange rounds of the ensemble (in-kernel exchange)
     const uint32_t k0 = (uint32_t)ed.seed, k1 = (uint32_t)(ed.seed >> 32);
     const uint32_t c3 = ed.ens_id | (kTagMove << 24);
     const bool ljb = ed.lj_bonded != 0;
@@ -510,6 +511,24 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
         }
         E = (E + (double)dsum.hi) + (double)dsum.lo;
         if (warp == 0) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
+        if (S.xin && ed.exchange_every > 0 && ed.R > 1 && (s + 1) % ed.exchange_every == 0) {
+            // the exchange round of this ensemble, inside the launch (warp 0); then the new slot
+            if (warp == 0) {
+                if (lane == 0) S.E[g] = E;
+                const bool ok = ensemble_exchange(S, rd.ens, g, ed.rep_base, ed.R, s + 1, xr, lane);
+                if (lane == 0) FIRST[3] = ok ? __ldcg(&S.temp_of_rep[g]) : -1;  // written by the first replica
+            }
+            __syncthreads();
+            const int ns = FIRST[3];
+            if (ns < 0) {
+                if (tid == 0) atomicOr(S.err, kErrTimeout);
+                s_end = s + 1;
+                break;
+            }
+            slot = ns;
+            gs = rd.slot_base + slot;
+            Tf = S.Tf[gs];
+        }
     }
     __syncthreads();
     for (int i = tid; i < N; i += T) S.pos[rd.pos_off + i] = P[i];
@@ -554,6 +573,56 @@ static cudaError_t configure_grp_w(int smem) {
     set(k_sweep_grp<16, W>);
     set(k_sweep_grp<32, W>);
     return e;
+}
+
+template <int W>
+static cudaError_t coop_grp_w(const State& s, int chunk, cudaStream_t st, size_t smem) {
+    State sc = s;
+    sc.xin = 1;
+    void* args[] = {&sc, &chunk};
+    const void* f = nullptr;
+    switch (reg_slots(s.nmax)) {
+        case 1: f = (const void*)k_sweep_grp<1, W>; break;
+        case 2: f = (const void*)k_sweep_grp<2, W>; break;
+        case 4: f = (const void*)k_sweep_grp<4, W>; break;
+        case 8: f = (const void*)k_sweep_grp<8, W>; break;
+        case 16: f = (const void*)k_sweep_grp<16, W>; break;
+        case 32: f = (const void*)k_sweep_grp<32, W>; break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaLaunchCooperativeKernel(f, dim3(s.n_reps), dim3(32 * W), args, smem, st);
+}
+
+template <int W>
+static bool fits_grp_w(int n_blocks, int nmax, size_t smem, int num_sms) {
+    int per_sm = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (reg_slots(nmax)) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_grp<1, W>, 32 * W, smem); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_grp<2, W>, 32 * W, smem); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_grp<4, W>, 32 * W, smem); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_grp<8, W>, 32 * W, smem); break;
+        case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_grp<16, W>, 32 * W, smem); break;
+        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_grp<32, W>, 32 * W, smem); break;
+        default: break;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (long long)per_sm * num_sms >= n_blocks;
+}
+
+bool grp_coop_fits(const State& s, int nmax, int num_sms) {
+    const int w = grp_warps(nmax);
+    const size_t smem = grp_smem_bytes(nmax, w);
+    return w == 4 ? fits_grp_w<4>(s.n_reps, nmax, smem, num_sms) : fits_grp_w<8>(s.n_reps, nmax, smem, num_sms);
+}
+
+cudaError_t launch_sweep_grp_coop(const State& s, int chunk, cudaStream_t st) {
+    const int w = grp_warps(s.nmax);
+    const size_t smem = grp_smem_bytes(s.nmax, w);
+    return w == 4 ? coop_grp_w<4>(s, chunk, st, smem) : coop_grp_w<8>(s, chunk, st, smem);
 }
 
 cudaError_t configure_sweep_grp(int nmax) {

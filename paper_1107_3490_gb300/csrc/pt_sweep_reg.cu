@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
     const EnsDev ed = S.ens[rd.ens];
     const int N = rd.N;
     int64_t s = S.rep_sweep[g];
-    const int64_t s_end = min(ed.target, s + (int64_t)chunk);
+    int64_t s_end = min(ed.target, s + (int64_t)chunk);
     if (s >= s_end) return;
 
     float4* P = smem;                                  // [nmax] the chain
@@ -66,9 +66,10 @@ __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
     __syncwarp();
 
     double E = S.E[g];
-    const int slot = S.temp_of_rep[g];
-    const int gs = rd.slot_base + slot;
-    const float Tf = S.Tf[gs];
+    int slot = S.temp_of_rep[g];
+    int gs = rd.slot_base + slot;
+    float Tf = S.Tf[gs];
+    int64_t xr = S.xin ? S.ens[rd.ens].xround : 0;  // exchange rounds of the ensemble (in-kernel exchange)
     const uint32_t k0 = (uint32_t)ed.seed, k1 = (uint32_t)(ed.seed >> 32);
     const uint32_t c3 = ed.ens_id | (kTagMove << 24);
     const bool ljb = ed.lj_bonded != 0;
@@ -268,6 +269,18 @@ __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
         }
         E = (E + (double)dsum.hi) + (double)dsum.lo;
         sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
+        if (S.xin && ed.exchange_every > 0 && ed.R > 1 && (s + 1) % ed.exchange_every == 0) {
+            // the exchange round of this ensemble, inside the launch; then the new slot
+            if (lane == 0) S.E[g] = E;
+            if (!ensemble_exchange(S, rd.ens, g, ed.rep_base, ed.R, s + 1, xr, lane)) {
+                if (lane == 0) atomicOr(S.err, kErrTimeout);
+                s_end = s + 1;
+                break;
+            }
+            slot = __ldcg(&S.temp_of_rep[g]);  // written by the ensemble's first replica
+            gs = rd.slot_base + slot;
+            Tf = S.Tf[gs];
+        }
     }
     __syncwarp();
     for (int j = lane; j < N; j += 32) S.pos[rd.pos_off + j] = P[j];
@@ -285,6 +298,50 @@ int reg_slots(int nmax) {
 
 size_t reg_smem_bytes(int nmax) {
     return (size_t)nmax * (sizeof(float4) + sizeof(int)) + (64 + 3 * kPend) * sizeof(float4);
+}
+
+template <int U>
+static cudaError_t coop_reg(const State& s, int chunk, cudaStream_t st, size_t smem) {
+    State sc = s;
+    sc.xin = 1;
+    void* args[] = {&sc, &chunk};
+    return cudaLaunchCooperativeKernel((const void*)k_sweep_reg<U>, dim3(s.n_reps), dim3(32), args, smem, st);
+}
+
+template <int U>
+static bool fits_reg(int n_blocks, size_t smem, int num_sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_reg<U>, 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (long long)per_sm * num_sms >= n_blocks;
+}
+
+bool reg_coop_fits(const State& s, int nmax, int num_sms) {
+    const size_t smem = reg_smem_bytes(nmax);
+    switch (reg_slots(nmax)) {
+        case 1: return fits_reg<1>(s.n_reps, smem, num_sms);
+        case 2: return fits_reg<2>(s.n_reps, smem, num_sms);
+        case 4: return fits_reg<4>(s.n_reps, smem, num_sms);
+        case 8: return fits_reg<8>(s.n_reps, smem, num_sms);
+        case 16: return fits_reg<16>(s.n_reps, smem, num_sms);
+        case 32: return fits_reg<32>(s.n_reps, smem, num_sms);
+        default: return false;
+    }
+}
+
+cudaError_t launch_sweep_reg_coop(const State& s, int chunk, cudaStream_t st) {
+    const size_t smem = reg_smem_bytes(s.nmax);
+    switch (reg_slots(s.nmax)) {
+        case 1: return coop_reg<1>(s, chunk, st, smem);
+        case 2: return coop_reg<2>(s, chunk, st, smem);
+        case 4: return coop_reg<4>(s, chunk, st, smem);
+        case 8: return coop_reg<8>(s, chunk, st, smem);
+        case 16: return coop_reg<16>(s, chunk, st, smem);
+        case 32: return coop_reg<32>(s, chunk, st, smem);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_sweep_reg(const State& s, int chunk, cudaStream_t st) {

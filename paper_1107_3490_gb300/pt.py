@@ -80,6 +80,8 @@ _SIGS = {
     "pt_energy_fp64": (_I, [_V, _V, _I, _I, _I, _V]),
     "pt_energy_fp64_noalloc": (_I, [_V, _I, _I, _I, _V, _V]),
     "pt_set_sweep_kernel": (_I, [_V, _I]),
+    "pt_set_launch_mode": (_I, [_V, _I]),
+    "pt_get_launch_mode": (_I, [_V]),
     "pt_get_sweep_kernel": (_I, [_V]),
     "pt_autotune": (_I, [_V, _I, _I, ctypes.POINTER(ctypes.c_int)]),
     "pt_set_kernel_timing": (_I, [_V, _I]),
@@ -347,8 +349,18 @@ def pt_energy_fp64_noalloc(conf_dev_ptr: int, N: int, n_conf: int, lj_bonded: in
 
 
 def pt_set_sweep_kernel(h, variant: int) -> None:
-    """0 warp per replica, 1 lookahead groups, 2 team of warps, 3 warp per move of a group."""
+    """0 warp per replica, 1 lookahead groups, 2 team of warps, 3 warp per move of a group,
+    4 chain in registers (N <= 1024), 5 CTA per replica, warp per move (N <= 1024)."""
     _ck(lib().pt_set_sweep_kernel(h, int(variant)))
+
+
+def pt_set_launch_mode(h, mode: int) -> None:
+    """1: persistent launch with in-kernel exchange where possible (default); 0: per-sweep launches."""
+    _ck(lib().pt_set_launch_mode(h, int(mode)))
+
+
+def pt_get_launch_mode(h) -> int:
+    return lib().pt_get_launch_mode(h)
 
 
 def pt_get_sweep_kernel(h) -> int:
@@ -356,7 +368,8 @@ def pt_get_sweep_kernel(h) -> int:
 
 
 def pt_autotune(h, trial_sweeps: int = 8, force: bool = False) -> int:
-    """Time every sweep kernel on h (state restored afterwards) and keep the fastest."""
+    """Time every sweep kernel (4 and 5 in both launch modes) on h, state restored
+    afterwards, and keep the fastest kernel and launch mode."""
     v = ctypes.c_int(-1)
     _ck(lib().pt_autotune(h, int(trial_sweeps), int(bool(force)), ctypes.byref(v)))
     return v.value
@@ -367,7 +380,7 @@ def pt_set_kernel_timing(h, on: bool) -> None:
 
 
 def pt_kernel_timing(h):
-    """(mean sweep-kernel launch ms over the latest recorded launches, launches covered)."""
+    """(mean sweep-kernel ms per sweep over the latest recorded launches, launches covered)."""
     ms, n = ctypes.c_double(), ctypes.c_int()
     _ck(lib().pt_kernel_timing(h, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value

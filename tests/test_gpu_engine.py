@@ -276,3 +276,70 @@ def test_the_move_log_does_not_change_the_chain(variant):
         assert np.array_equal(a["E"], b["E"])
     for x, y in zip(a["acc"], b["acc"]):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("variant", [4, 5])
+@pytest.mark.parametrize("xe", [1, 3])
+def test_persistent_launch_runs_the_same_chain(variant, xe):
+    """One cooperative launch with the exchange rounds inside the kernel against per-sweep
+    launches with a separate exchange kernel: the same chain, bit for bit, including over
+    several calls and with ensembles of different sizes in one context."""
+    specs = [(60, 8, 1, 0), (90, 5, 2, 1), (30, 12, 3, 2)]
+    out = []
+    for mode in (1, 0):
+        made = [pt.make_params(N, inputs.temperature_ladder(0.2, 3.0, R), s, ensemble_id=e,
+                               init_positions=inputs.random_coil(N, R, s, e), n_bins=128, recompute_every=7)
+                for (N, R, s, e) in specs]
+        h = pt.pt_create_batch([p for p, _ in made])
+        try:
+            pt.pt_set_sweep_kernel(h, variant)
+            pt.pt_set_launch_mode(h, mode)
+            assert pt.pt_get_launch_mode(h) == mode
+            for n in (11, 1, 20):
+                pt.pt_sweep(h, n, xe)
+            out.append(_state(h) + (pt.pt_observables(h), [pt.pt_counters(h, e) for e in range(3)]))
+        finally:
+            pt.pt_destroy(h)
+    a, b = out
+    _same(a[:5], b[:5])
+    for x, y in zip(a[5], b[5]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a[6], b[6]) and a[7] == b[7]
+
+
+def test_persistent_launch_continues_from_a_checkpoint():
+    """The in-kernel exchange barrier's counters follow a restore."""
+    h = _make(N=50, R=6, seed=12)
+    try:
+        pt.pt_set_sweep_kernel(h, 4)
+        pt.pt_sweep(h, 9, 1)
+        host = np.zeros(pt.pt_checkpoint_size(h), dtype=np.uint8)
+        n = pt.pt_checkpoint_into(h, host)
+        pt.pt_sweep(h, 13, 1)
+        after = _state(h)
+        pt.pt_restore_from(h, host, n)
+        pt.pt_sweep(h, 13, 1)
+        _same(_state(h), after)
+    finally:
+        pt.pt_destroy(h)
+
+
+@pytest.mark.parametrize("variant,mode,xe", [(4, 1, 1), (5, 1, 3), (5, 0, 1), (2, 0, 1), (2, 0, 4)])
+def test_kernel_timing_in_every_launch_path(variant, mode, xe):
+    """Kernel timing brackets persistent launches, graph replays and direct launches alike,
+    and does not change the chain."""
+    out = []
+    for timing in (True, False):
+        h = _make(N=60, R=8, seed=21)
+        try:
+            pt.pt_set_sweep_kernel(h, variant)
+            pt.pt_set_launch_mode(h, mode)
+            pt.pt_set_kernel_timing(h, timing)
+            pt.pt_sweep(h, 12, xe)
+            if timing:
+                ms, n = pt.pt_kernel_timing(h)
+                assert n >= 1 and ms > 0.0 and math.isfinite(ms)
+            out.append(_state(h))
+        finally:
+            pt.pt_destroy(h)
+    _same(out[0], out[1])

@@ -281,6 +281,10 @@ def run_gpu(args):
     if clocks and clocks.get("sm_mhz"):
         roofline["frac_at_measured_clock"] = achieved / fp32_peak_tflops(num_sms, clocks["sm_mhz"])
     pt.pt_destroy(h)
+    # measured FP32 FMA throughput of this GPU (independent fmaf chains on every warp slot)
+    fma_tflops, _ = pt.pt_fp32_fma_rate(stream.cuda_stream)
+    roofline["peak_measured_fma"] = fma_tflops
+    roofline["frac_of_measured_fma"] = achieved / fma_tflops
 
     # every step: the target-setting launch, then one cooperative launch (persistent mode)
     # or graphs of 32 (sweep, exchange) launch pairs

@@ -268,6 +268,14 @@ int pt_get_launch_mode(const pt_ctx* h);
 int pt_set_kernel_timing(pt_ctx* h, int on);
 int pt_kernel_timing(pt_ctx* h, double* mean_sweep_ms, int* n_launches);
 
+/* Measured FP32 FMA throughput of the current device, the measured counterpart of the derived
+ * FP32 peak (SMs x 128 lanes x 2 flops x clock) used for the sweep kernels' roofline: one
+ * kernel of 4 blocks of 512 threads per SM, each thread running 8 independent fmaf chains for
+ * trips x 16 steps, timed with CUDA events on `stream` (NULL: default stream) after a shorter
+ * warm-up launch. *tflops = 2 x FMAs / time; *ms (may be NULL) = the timed launch. Allocates
+ * and frees a small output buffer; synchronises the stream. trips ~ 50000 runs ~50 ms. */
+int pt_fp32_fma_rate(void* stream, int trips, double* tflops, double* ms);
+
 /* Checkpoint of the whole state (positions, energies, labels, counters, histograms,
  * moments, acceptance). With buf == NULL only *size is set. pt_restore needs a context
  * created with the same shapes and parameters. The random stream is counter-based, so a

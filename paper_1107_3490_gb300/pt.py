@@ -86,6 +86,7 @@ _SIGS = {
     "pt_autotune": (_I, [_V, _I, _I, ctypes.POINTER(ctypes.c_int)]),
     "pt_set_kernel_timing": (_I, [_V, _I]),
     "pt_kernel_timing": (_I, [_V, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "pt_fp32_fma_rate": (_I, [_V, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "pt_server_config_init": (None, [ctypes.POINTER(pt_server_config), _I, ctypes.c_size_t]),
     "pt_server_create": (_V, [ctypes.POINTER(pt_server_config), _V]),
     "pt_server_submit": (_I64, [_V, ctypes.POINTER(pt_params), _I64, _I]),
@@ -384,6 +385,13 @@ def pt_kernel_timing(h):
     ms, n = ctypes.c_double(), ctypes.c_int()
     _ck(lib().pt_kernel_timing(h, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def pt_fp32_fma_rate(stream: int = 0, trips: int = 50000):
+    """(measured FP32 FMA TFLOP/s of the current device, ms of the timed launch)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _ck(lib().pt_fp32_fma_rate(stream or None, int(trips), ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
 
 
 def pt_checkpoint_into(h, buf) -> int:

@@ -343,3 +343,16 @@ def test_kernel_timing_in_every_launch_path(variant, mode, xe):
         finally:
             pt.pt_destroy(h)
     _same(out[0], out[1])
+
+
+def test_fp32_fma_rate_is_near_the_derived_peak():
+    """The measured FMA throughput lies between a third of and just above the derived FP32
+    peak (SMs x 128 lanes x 2 flops x the maximum SM clock)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    derived = sms * 128 * 2 * 2.2e9 / 1e12  # above any boost clock of the part
+    tflops, ms = pt.pt_fp32_fma_rate(0, 5000)
+    assert ms > 0.0
+    assert derived / 3 < tflops < derived, (tflops, derived)
+    with pytest.raises(pt.PtError):
+        pt.pt_fp32_fma_rate(0, 0)

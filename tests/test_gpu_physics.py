@@ -1,11 +1,19 @@
-"""Physics of the 13-mer (Sec. 4.1): the specific-heat peak of the freezing transition.
+"""Physics of the 13-mer and the 55-mer (Sec. 4.1): the specific-heat peaks of the freezing
+transition and the Theta collapse.
 
 The paper reports the low-temperature C_V/N peak of the 13-bead chain at T ~ 0.33, with the
 d<r_gyr^2>/dT peak close to it. A PT run on the GPU (32 replicas, T 0.15-2.0, 4e5 sweeps,
 exchange every sweep), reweighted with the library's multiple-histogram method, must put
 the C_V/N peak at 0.31-0.36 with LJ between all pairs (Eq. 4 read literally). With LJ only
 between non-bonded pairs the same run puts the peak clearly lower (about 0.30), which is
-why the library's default counts LJ for bonded pairs too."""
+why the library's default counts LJ for bonded pairs too.
+
+The 55-mer freezes at T ~ 0.32 in the paper, with the Theta collapse near T ~ 1.5. Four
+independent ensembles of 64 replicas (T 0.22-2.0), 4e6 sweeps each with a displacement
+half-width of 0.1 (0.3 leaves the cold replicas in amorphous globules: the peak then sits
+near 0.26 with <E>/N ~ -4.36 at T = 0.2), reweighted together, must put the low-T C_V/N
+peak at 0.30-0.34 (each ensemble on its own within 0.29-0.35) and the high-T peak of
+d<r_gyr^2>/dT at 1.4-1.8."""
 import numpy as np
 import pytest
 
@@ -46,3 +54,37 @@ def test_13mer_peak_moves_without_bonded_lj():
     t_cv, _, _ = _peak(0)
     print(f"LJ between non-bonded pairs only: C_V/N peak at T={t_cv:.3f}")
     assert t_cv < 0.315
+
+
+def test_55mer_freezing_and_collapse():
+    N, R, NE, sweeps = 55, 64, 4, 4000000
+    T = inputs.temperature_ladder(0.22, 2.0, R)
+    e_min, e_max, nb = -6.0 * N, 3.0 * N, 8192
+    made = [pt.make_params(N, T, 11 + e, ensemble_id=e, init_positions=inputs.random_coil(N, R, 11 + e, e),
+                           delta=0.1, n_bins=nb, e_min=e_min, e_max=e_max, n_therm=sweeps // 10)
+            for e in range(NE)]
+    h = pt.pt_create_batch([p for p, _ in made])
+    try:
+        pt.pt_autotune(h, 50)
+        for _ in range(8):
+            pt.pt_sweep(h, sweeps // 8, 1)
+        H = pt.pt_histograms(h).reshape(NE, R, nb)
+        rg, _ = pt.pt_obs_histograms(h, NE * R * nb)
+        rg = rg.reshape(NE, R, nb)
+        assert pt.pt_hist_outliers(h).sum() == 0
+    finally:
+        pt.pt_destroy(h)
+    Tq = np.linspace(0.22, 2.0, 357)
+    low, high = Tq < 0.7, Tq > 0.8
+
+    def peaks(HH, RG):
+        ln_g, f, it = pt.pt_wham(T, HH, e_min, e_max, tol=1e-10, max_iter=500000)
+        c = pt.pt_wham_canonical(ln_g, e_min, e_max, Tq, RG.sum(0), HH.sum(0))
+        return Tq[low][np.argmax(c[low, 1])], Tq[high][np.argmax(c[high, 3])]
+
+    t_cv, t_theta = peaks(H.sum(0), rg.sum(0))
+    each = [peaks(H[e], rg[e])[0] for e in range(NE)]
+    print(f"55-mer: C_V/N peak at T={t_cv:.3f} (ensembles {each}); d<rg2>/dT high-T peak at T={t_theta:.3f}")
+    assert 0.30 <= t_cv <= 0.34
+    assert all(0.29 <= t <= 0.35 for t in each)
+    assert 1.4 <= t_theta <= 1.8

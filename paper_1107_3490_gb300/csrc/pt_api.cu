@@ -196,7 +196,7 @@ void free_state(pt_ctx* h) {
     State& S = h->S;
     void* ptrs[] = {S.reps, S.ens, S.pos, S.E, S.temp_of_rep, S.rep_of_temp, S.Tf, S.beta, S.hist,
                     S.outl, S.mom, S.obs, S.obs_rg2_hist, S.obs_ree2_hist, S.mv_att, S.mv_acc, S.ex_att,
-                    S.ex_acc, S.drift, S.rep_sweep, S.err, S.xarrive, S.xdone, S.log_bead, S.log_de, S.log_theta, S.log_acc,
+                    S.ex_acc, S.drift, S.rep_sweep, S.err, S.xarrive, S.xE, S.log_bead, S.log_de, S.log_theta, S.log_acc,
                     S.log_e, S.log_x, h->scratch, h->conf_buf, h->eout_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -380,7 +380,7 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     A(dalloc(&S.rep_sweep, G));
     A(dalloc(&S.err, 1));
     A(dalloc(&S.xarrive, (size_t)n_ens));
-    A(dalloc(&S.xdone, (size_t)n_ens));
+    A(dalloc(&S.xE, 2 * G));
     if (a != cudaSuccess) {
         fail(a == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA, "device allocation: %s", cudaGetErrorString(a));
         pt_destroy(h);
@@ -1108,14 +1108,10 @@ extern "C" int pt_restore(pt_ctx* h, const void* buf, size_t size) {
         CK(h, cudaMemcpy(b.dev, p, b.bytes, cudaMemcpyHostToDevice));
         p += b.bytes;
     }
-    // the in-kernel exchange barrier counts R arrivals and one release per round
-    std::vector<unsigned long long> arr(eds.size()), rel(eds.size());
-    for (size_t e = 0; e < eds.size(); ++e) {
-        rel[e] = (unsigned long long)eds[e].xround;
-        arr[e] = rel[e] * (unsigned long long)eds[e].R;
-    }
+    // the in-kernel exchange barrier counts R arrivals per round
+    std::vector<unsigned long long> arr(eds.size());
+    for (size_t e = 0; e < eds.size(); ++e) arr[e] = (unsigned long long)eds[e].xround * (unsigned long long)eds[e].R;
     CK(h, cudaMemcpy(h->S.xarrive, arr.data(), arr.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->S.xdone, rel.data(), rel.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
     h->done = (int64_t)hdr[2];
     return PT_OK;
 }

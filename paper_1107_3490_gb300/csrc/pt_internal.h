@@ -55,9 +55,10 @@ struct State {
     int64_t* rep_sweep;       // [replica] sweeps done
     int* err;                 // error bits
     // in-kernel exchange of persistent launches: per ensemble, arrivals at the ensemble
-    // barrier (R per round) and rounds released; xin != 0 in such a launch
+    // barrier (R per round); energies published by slot, two buffers by round parity
+    // ([2][replica]); xin != 0 in such a launch
     unsigned long long* xarrive;
-    unsigned long long* xdone;
+    double* xE;
     int xin;
     // per-move log of sweeps [log_s0, log_s0 + log_ns); null pointers when off
     int64_t log_s0, log_ns, log_pstride;  // log_pstride = total positions

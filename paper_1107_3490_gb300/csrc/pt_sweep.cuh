@@ -42,37 +42,64 @@ static __device__ double warp_full_energy(const float4* P, int N, int lj_bonded,
 }
 
 
-// Shape observables of the chain in shared memory (Sec. 4.1), in FP64 by one warp: the
-// squared radius of gyration (Eq. 8; centre of mass first, then the mean squared distance
-// from it) and the squared end-to-end distance. Results in every lane.
-__device__ __forceinline__ void warp_shape(const float4* P, int N, int lane, double& rg2, double& ree2) {
-    double cx = 0.0, cy = 0.0, cz = 0.0;
-    for (int i = lane; i < N; i += 32) {
-        const float4 q = P[i];
-        cx += q.x;
-        cy += q.y;
-        cz += q.z;
-    }
-    cx = warp_sum_d(cx) / N;
-    cy = warp_sum_d(cy) / N;
-    cz = warp_sum_d(cz) / N;
-    double g = 0.0;
-    for (int i = lane; i < N; i += 32) {
-        const float4 q = P[i];
-        const double dx = q.x - cx, dy = q.y - cy, dz = q.z - cz;
-        g += dx * dx + dy * dy + dz * dz;
-    }
-    rg2 = warp_sum_d(g) / N;
-    const float4 a = P[0], b = P[N - 1];
-    const double ex = (double)b.x - a.x, ey = (double)b.y - a.y, ez = (double)b.z - a.z;
-    ree2 = ex * ex + ey * ey + ez * ez;
+// Double-float warp sum (every lane gets the same value: df_add is commutative).
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+    for (int m = 16; m; m >>= 1)
+        v = df_add(v, df{__shfl_xor_sync(kFull, v.hi, m), __shfl_xor_sync(kFull, v.lo, m)});
+    return v;
 }
 
-// One exchange round of ensemble e (Sec. 3.3, Eq. 6) by one warp: the pairs (t, t+1) of the
-// round's parity on different lanes (disjoint, so labels swap without conflicts). sw is the
-// ensemble's sweep count after the sweep the round follows. Accept iff u < exp(arg) in FP64.
+// Shape observables of the chain in shared memory (Sec. 4.1) by one warp: the squared
+// radius of gyration (Eq. 8; centre of mass first, then the mean squared distance from it)
+// and the squared end-to-end distance. Double-float arithmetic on the FP32 pipe (relative
+// error ~1e-13; the FP64 pipe of this GPU is ~64 times slower), results in every lane.
+__device__ __forceinline__ void warp_shape(const float4* P, int N, int lane, double& rg2, double& ree2) {
+    df cx = {0.f, 0.f}, cy = {0.f, 0.f}, cz = {0.f, 0.f};
+    for (int i = lane; i < N; i += 32) {
+        const float4 q = P[i];
+        cx = df_add(cx, df{q.x, 0.f});
+        cy = df_add(cy, df{q.y, 0.f});
+        cz = df_add(cz, df{q.z, 0.f});
+    }
+    const df n = {(float)N, 0.f};  // exact: N < 2^24
+    cx = df_div(warp_sum_df(cx), n);
+    cy = df_div(warp_sum_df(cy), n);
+    cz = df_div(warp_sum_df(cz), n);
+    df g = {0.f, 0.f};
+    for (int i = lane; i < N; i += 32) {
+        const float4 q = P[i];
+        const df dx = df_sub(df{q.x, 0.f}, cx), dy = df_sub(df{q.y, 0.f}, cy), dz = df_sub(df{q.z, 0.f}, cz);
+        g = df_add(g, df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz)));
+    }
+    const df r = df_div(warp_sum_df(g), n);
+    rg2 = (double)r.hi + (double)r.lo;
+    const float4 a = P[0];
+    const df e = r2_df(P[N - 1], make_float3(a.x, a.y, a.z));  // exact differences and squares
+    ree2 = (double)e.hi + (double)e.lo;
+}
+
+// Exchange decision of pair (t, t+1) (Eq. 6): accept iff u < exp(arg), arg = (E_t - E_t+1)
+// (beta_t - beta_t+1), exactly as in FP64, with u = w 2^-24 (w < 2^24). arg >= 0 accepts
+// (exp >= 1 > u). Below -20 exp(arg) < 2^-24, under every u > 0. Otherwise expf of the
+// rounded argument (within 2 ulp) decides when u lies clear of the band that the argument's
+// rounding and expf's error leave around exp(arg); inside the band FP64 exp decides.
+__device__ __forceinline__ bool exchange_accept(double arg, uint32_t w) {
+    if (arg >= 0.0) return true;
+    const float uf = (float)w * 5.9604644775390625e-08f;  // exact
+    if (arg < -20.0) return w == 0u && exp(arg) > 0.0;
+    const float af = (float)arg;
+    const float ef = expf(af);
+    const float m = __fmul_ru(__fadd_ru(fabsf(af), 8.f), 1.1920929e-07f);  // (|af| + 8) 2^-23
+    if (uf < __fmul_rd(ef, __fsub_rd(1.f, m))) return true;
+    if (uf > __fmul_ru(ef, __fadd_ru(1.f, m))) return false;
+    return (double)uf < exp(arg);
+}
+
+// One exchange round of ensemble e (Sec. 3.3, Eq. 6) by one warp of the exchange kernel: the
+// pairs (t, t+1) of the round's parity on different lanes (disjoint, so labels swap without
+// conflicts). sw is the ensemble's sweep count after the sweep the round follows.
 __device__ __forceinline__ void exchange_round_warp(const State& S, int e, int64_t sw, int lane) {
-    // reads of what other blocks of a persistent launch wrote bypass L1 (__ldcg)
     EnsDev* ed = S.ens + e;
     const int base = ed->rep_base, R = ed->R;
     const int64_t x = __ldcg(&ed->xround);
@@ -89,8 +116,7 @@ __device__ __forceinline__ void exchange_round_warp(const State& S, int e, int64
         const int ra = __ldcg(&S.rep_of_temp[base + t]), rb = __ldcg(&S.rep_of_temp[base + t + 1]);
         const double arg = (__ldcg(&S.E[base + ra]) - __ldcg(&S.E[base + rb])) * (S.beta[base + t] - S.beta[base + t + 1]);
         const u4 w = philox(u4{(uint32_t)t, (uint32_t)x, 0u, ed->ens_id | (kTagExch << 24)}, k0, k1);
-        const double u = (double)(w.x >> 8) * (1.0 / 16777216.0);
-        const bool acc = u < exp(arg);
+        const bool acc = exchange_accept(arg, w.x >> 8);
         S.ex_att[base + t] += 1ull;
         if (acc) {
             S.ex_acc[base + t] += 1ull;
@@ -109,7 +135,7 @@ __device__ __forceinline__ void exchange_round_warp(const State& S, int e, int64
 }
 
 // Bounded wait (lane 0 polls, the warp waits) until *p >= target; false if it gave up. A
-// poll costs at least 100 ns, so the limit is about a second or more, far above one sweep.
+// poll costs an L2 round trip plus 32 ns, so the limit is seconds, far above one sweep.
 constexpr long long kWaitPolls = 1ll << 23;
 __device__ __forceinline__ bool wait_at_least(unsigned long long* p, unsigned long long target, int lane) {
     int ok = 1;
@@ -120,37 +146,68 @@ __device__ __forceinline__ bool wait_at_least(unsigned long long* p, unsigned lo
                 ok = 0;
                 break;
             }
-            __nanosleep(100);
+            __nanosleep(32);
         }
         __threadfence();
     }
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-// In-kernel exchange after sweep count sw, called by one warp of every replica of ensemble e
-// once that replica's energy S.E[g] is stored: the replica arrives at the ensemble barrier;
-// the ensemble's first replica waits for all R arrivals, runs the round and releases it;
-// the others wait for the release. xr counts the ensemble's rounds (the same in every
-// replica). False if a wait gave up.
-__device__ __forceinline__ bool ensemble_exchange(const State& S, int e, int g, int rep_base, int R, int64_t sw,
-                                                  int64_t& xr, int lane) {
+// In-kernel exchange after sweep count sw (persistent launches; one warp of every replica of
+// ensemble e calls it, lane 0 does the work). The replica publishes its energy under its
+// temperature slot in the round's buffer (xE, two buffers by round parity), arrives at the
+// ensemble barrier (R arrivals per round) and waits for all R. Then it decides its own pair
+// of the round from the two published energies, the same decision the pair's other replica
+// and the exchange kernel take, and moves to its new slot. The pair's lower replica keeps
+// the pair counters and the log; each replica writes its own labels; replica 0 of the
+// ensemble advances xround. No replica reads the label arrays inside the launch, and a
+// buffer is rewritten two rounds later, after every replica has passed the round between.
+// slot (local) is updated; false if the wait gave up.
+__device__ __forceinline__ bool ensemble_exchange(const State& S, const EnsDev& ed, int e, int g, int r, double E,
+                                                  int64_t sw, int64_t& xr, int& slot, int lane) {
+    const int base = ed.rep_base, R = ed.R;
+    double* buf = S.xE + (size_t)(xr & 1) * S.n_reps + base;
     if (lane == 0) {
+        __stcg(buf + slot, E);
         __threadfence();
         atomicAdd(&S.xarrive[e], 1ull);
     }
-    bool ok;
-    if (g == rep_base) {
-        ok = wait_at_least(&S.xarrive[e], (unsigned long long)R * (unsigned long long)(xr + 1), lane);
-        if (ok) {
-            exchange_round_warp(S, e, sw, lane);
-            __threadfence();
-            if (lane == 0) atomicExch(&S.xdone[e], (unsigned long long)(xr + 1));
+    const bool ok = wait_at_least(&S.xarrive[e], (unsigned long long)R * (unsigned long long)(xr + 1), lane);
+    if (!ok) return false;
+    int ns = slot;
+    if (lane == 0) {
+        const int q = (int)(xr & 1);
+        const bool lower = ((slot - q) & 1) == 0 && slot >= q && slot + 1 < R;
+        const bool upper = ((slot - q) & 1) != 0 && slot >= q + 1;
+        const int64_t s_log = sw - 1;
+        int8_t* xo = (S.log_x && s_log >= S.log_s0 && s_log < S.log_s0 + S.log_ns)
+                         ? S.log_x + (size_t)(s_log - S.log_s0) * S.n_reps + base
+                         : nullptr;
+        if (lower || upper) {
+            const int t = lower ? slot : slot - 1;
+            const double arg = (__ldcg(buf + t) - __ldcg(buf + t + 1)) * (S.beta[base + t] - S.beta[base + t + 1]);
+            const u4 w = philox(u4{(uint32_t)t, (uint32_t)xr, 0u, ed.ens_id | (kTagExch << 24)}, (uint32_t)ed.seed,
+                                (uint32_t)(ed.seed >> 32));
+            const bool acc = exchange_accept(arg, w.x >> 8);
+            if (acc) ns = lower ? t + 1 : t;
+            if (lower) {
+                S.ex_att[base + t] += 1ull;
+                if (acc) S.ex_acc[base + t] += 1ull;
+            }
+            if (xo) xo[slot] = lower ? (acc ? 1 : 0) : -1;
+        } else if (xo) {
+            xo[slot] = -1;
         }
-    } else {
-        ok = wait_at_least(&S.xdone[e], (unsigned long long)(xr + 1), lane);
+        S.rep_of_temp[base + ns] = r;
+        S.temp_of_rep[g] = ns;
+        if (r == 0) {
+            S.ens[e].xround = xr + 1;
+            S.ens[e].last_x_sweep = sw;
+        }
     }
+    slot = __shfl_sync(0xffffffffu, ns, 0);
     ++xr;
-    return ok;
+    return true;
 }
 
 // End of one sweep of replica g (all lanes of its warp call it): the periodic FP64

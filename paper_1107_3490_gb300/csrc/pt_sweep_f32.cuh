@@ -20,14 +20,16 @@ constexpr float kEdge = 1.0e-5f;         // bond lengths this close to the FENE 
 // Bonded partner q of the moved bead in FP32: FENE (Eq. 3) plus, if lj, the LJ term, with a
 // bound e on the rounding error. inexact: the accurate value needs double-float (a bond
 // length at least 0.2 from r0, or a steep LJ term); edge: a bond length within kEdge of the
-// FENE wall, where FP32 cannot tell whether the bond breaks.
+// FENE wall, where FP32 cannot tell whether the bond breaks; low_only: t - e is a lower
+// bound of the term but t + e is no upper bound (a new bond so close to the wall that the
+// first-order bound of log1p does not hold; the move can still be rejected for certain).
 struct BondF {
     float t, e;
-    bool inexact, edge;
+    bool inexact, edge, low_only;
 };
 __device__ __forceinline__ BondF bond_f32(float4 q, float3 p, float3 pn, bool lj) {
     const float R = (float)kRF;
-    BondF b = {0.f, 0.f, false, false};
+    BondF b = {0.f, 0.f, false, false, false};
     const float r2o = r2_f32(q, p), r2n = r2_f32(q, pn);
     const float ro = __fsqrt_rn(r2o), rn = __fsqrt_rn(r2n);
     const float uo = __fsub_rn(ro, (float)kR0), un = __fsub_rn(rn, (float)kR0);
@@ -58,12 +60,23 @@ __device__ __forceinline__ BondF bond_f32(float4 q, float3 p, float3 pn, bool lj
     const float e_wo = 2.f * R * (e_u + 2.e-8f) + 4.f * kEps0 * wo;
     const float e_z = (e_drr * fabsf(usum) + fabsf(drr) * (2.f * e_u + kEps0)) / wo + fabsf(z) * (e_wo / wo + 4.f * kEps0);
     const float den = 1.f + z - e_z;
-    if (!(den > 0.05f)) {  // log1p too steep here for this simple bound
-        b.edge = true;
-        return b;
+    float e, t;
+    if (!(den > 0.05f)) {
+        // log1p too steep here for the first-order bound. One side still holds: the term
+        // -c log(1 + z) falls as its argument grows, so -c log(a) with a >= 1 + z (z's
+        // bound taken 1.5-fold, rounded up) is a lower bound; logf is within 1 ulp, so its
+        // value plus 4 ulp of it bounds log(a) from above. The FP32 value is that bound.
+        const float a = __fadd_ru(__fadd_ru(1.f, z), 1.5f * e_z);
+        const float L = logf(a);
+        const float Lu = __fadd_ru(L, __fmaf_ru(fabsf(L), 4.f * 1.1920929e-7f, 1e-30f));
+        t = Lu <= 0.f ? __fmul_rd((float)kFeneC, -Lu) : -__fmul_ru(1.80000019f, Lu);  // 1.8f < 1.8 < 1.80000019f
+        e = 0.f;
+        b.low_only = true;
+        b.inexact = true;
+    } else {
+        e = 1.5f * (1.8f * e_z / den + 4.f * kEps0 * fabsf(tf)) + 1e-9f;
+        t = tf;
     }
-    float e = 1.5f * (1.8f * e_z / den + 4.f * kEps0 * fabsf(tf)) + 1e-9f;
-    float t = tf;
     if (lj) {
         const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
         const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
@@ -76,6 +89,11 @@ __device__ __forceinline__ BondF bond_f32(float4 q, float3 p, float3 pn, bool lj
     b.t = t;
     b.e = e + kEps0 * fabsf(t);
     return b;
+}
+
+// BondF flags packed for the move tables: bit 0 inexact, bit 1 edge, bit 2 lower bound only.
+__device__ __forceinline__ unsigned bond_flags(const BondF& b) {
+    return (b.inexact ? 1u : 0u) | (b.edge ? 2u : 0u) | (b.low_only ? 4u : 0u);
 }
 
 }  // namespace

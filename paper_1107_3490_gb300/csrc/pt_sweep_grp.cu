@@ -56,7 +56,7 @@ __device__ __forceinline__ void correction_f32(float4 qo, float4 qn, float3 p, f
         // the difference of two FENE terms can cancel far below their size: its value is
         // always taken in double-float (the bound still serves the decision)
         const BondF a = bond_f32(qn, p, pn, ljb), b = bond_f32(qo, p, pn, ljb);
-        fl = 1u | ((a.edge || b.edge) ? 2u : 0u);
+        fl = 1u | ((a.edge || b.edge || a.low_only || b.low_only) ? 2u : 0u);
         d = __fsub_rn(a.t, b.t);  // +inf when the new bond breaks
         e = __fadd_ru(__fadd_ru(a.e, b.e), 2.f * kEps0 * fabsf(d) < __int_as_float(0x7f800000) ? 2.f * kEps0 * fabsf(d) : 0.f);
     } else {
@@ -170,13 +170,13 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                     const BondF a = bond_f32(P[km - 1], pk, pnk, ljb);
                     bt = a.t;
                     be = a.e;
-                    bfl |= (a.inexact ? 1u : 0u) | (a.edge ? 2u : 0u);
+                    bfl |= bond_flags(a);
                 }
                 if (km + 1 < N) {
                     const BondF c = bond_f32(P[km + 1], pk, pnk, ljb);
                     bt = __fadd_rn(bt, c.t);
                     be = __fadd_rn(be, c.e);
-                    bfl |= (c.inexact ? 1u : 0u) | (c.edge ? 2u : 0u);
+                    bfl |= bond_flags(c);
                 }
                 D0[tid] = make_float4(__int_as_float(km | (int)(bfl << 16)), sx, sy, sz);
                 D1[tid] = make_float4(th, bt, be, 0.f);
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                             const BondF x = bond_f32(P[j], p, pn, ljb);
                             bnd = x.t;
                             bnde = x.e;
-                            bf = (x.inexact ? 1u : 0u) | (x.edge ? 2u : 0u);
+                            bf = bond_flags(x);
                         }
                     }
                     part = __fadd_rn(__fadd_rn(rs.aord, rs.ast), bnd);
@@ -244,13 +244,13 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                     const float el = __fmaf_rn(kDeltaX, rs.sw, __fmaf_rn(sum_err, __fadd_rn(rs.sab, bab), bnde));
                     const float lb = __fsub_rd(part, el), ub = __fadd_ru(part, el);
                     const bool lo_bad = !(lb >= -kQMax) || (bf & 2u);
-                    const bool hi_bad = !(ub <= kQMax) || (bf & 2u);
+                    const bool hi_bad = !(ub <= kQMax) || (bf & 6u);
                     const int ql = lo_bad ? 0 : __float2int_rd(__fmul_rd(fminf(lb, kQMax), kQ));
                     const int qh = hi_bad ? 0 : __float2int_ru(__fmul_ru(fmaxf(ub, -kQMax), kQ));
                     const int sl = __reduce_add_sync(kFull, ql);
                     const int sh = __reduce_add_sync(kFull, qh);
                     mfl = __reduce_or_sync(kFull, (lo_bad ? 1u : 0u) | (hi_bad ? 2u : 0u) | (rs.stm ? 4u : 0u) |
-                                                      ((bf & 3u) ? 8u : 0u));
+                                                      ((bf & 7u) ? 8u : 0u));
                     // corrections for accepted earlier group moves: lane l < i
                     if (lane < i) {
                         const int l = lane;
@@ -514,9 +514,9 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
         if (S.xin && ed.exchange_every > 0 && ed.R > 1 && (s + 1) % ed.exchange_every == 0) {
             // the exchange round of this ensemble, inside the launch (warp 0); then the new slot
             if (warp == 0) {
-                if (lane == 0) S.E[g] = E;
-                const bool ok = ensemble_exchange(S, rd.ens, g, ed.rep_base, ed.R, s + 1, xr, lane);
-                if (lane == 0) FIRST[3] = ok ? __ldcg(&S.temp_of_rep[g]) : -1;  // written by the first replica
+                int sl = slot;
+                const bool ok = ensemble_exchange(S, ed, rd.ens, g, rd.r, E, s + 1, xr, sl, lane);
+                if (lane == 0) FIRST[3] = ok ? sl : -1;
             }
             __syncthreads();
             const int ns = FIRST[3];

@@ -100,18 +100,18 @@ __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
                 const float3 pnk = make_float3(__fadd_rn(q.x, __fmul_rn(delta, sx)), __fadd_rn(q.y, __fmul_rn(delta, sy)),
                                                __fadd_rn(q.z, __fmul_rn(delta, sz)));
                 float bt = 0.f, be = 0.f;
-                unsigned bfl = 0u;  // bit 0: inexact, bit 1: edge
+                unsigned bfl = 0u;  // bond_flags: bit 0 inexact, bit 1 edge, bit 2 lower bound only
                 if (km > 0) {
                     const BondF a = bond_f32(P[km - 1], pk, pnk, ljb);
                     bt = a.t;
                     be = a.e;
-                    bfl |= (a.inexact ? 1u : 0u) | (a.edge ? 2u : 0u);
+                    bfl |= bond_flags(a);
                 }
                 if (km + 1 < N) {
                     const BondF c = bond_f32(P[km + 1], pk, pnk, ljb);
                     bt = __fadd_rn(bt, c.t);
                     be = __fadd_rn(be, c.e);
-                    bfl |= (c.inexact ? 1u : 0u) | (c.edge ? 2u : 0u);
+                    bfl |= bond_flags(c);
                 }
                 D0[lane] = make_float4(__int_as_float(km | (int)(bfl << 16)), sx, sy, sz);
                 D1[lane] = make_float4(th, bt, be, 0.f);
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
                         const BondF x = bond_f32(P[j], p, pn, ljb);
                         bnd = x.t;
                         bnde = x.e;
-                        bf = (x.inexact ? 1u : 0u) | (x.edge ? 2u : 0u);
+                        bf = bond_flags(x);
                     }
                 }
                 // ---- exact fixed-point warp sums of lower and upper bounds of the shares
@@ -171,13 +171,13 @@ __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
                 // a bound is clamped only in the direction that keeps it a bound; a share
                 // beyond the other side (or NaN, or a bond at the FENE wall) voids that sum
                 const bool lo_bad = !(lb >= -kQMax) || (bf & 2u);
-                const bool hi_bad = !(ub <= kQMax) || (bf & 2u);
+                const bool hi_bad = !(ub <= kQMax) || (bf & 6u);
                 const int ql = lo_bad ? 0 : __float2int_rd(__fmul_rd(fminf(lb, kQMax), kQ));
                 const int qh = hi_bad ? 0 : __float2int_ru(__fmul_ru(fmaxf(ub, -kQMax), kQ));
                 const int sl = __reduce_add_sync(kFull, ql);
                 const int sh = __reduce_add_sync(kFull, qh);
                 const unsigned fl = __reduce_or_sync(kFull, (lo_bad ? 1u : 0u) | (hi_bad ? 2u : 0u) |
-                                                                (rs.stm ? 4u : 0u) | ((bf & 3u) ? 8u : 0u));
+                                                                (rs.stm ? 4u : 0u) | ((bf & 7u) ? 8u : 0u));
                 // ---- decision (Eq. 5): certain unless theta lies inside [lower, upper]
                 bool accept = false, sure = false;
                 if (!(fl & 1u) && __fmul_rd(__int2float_rd(sl), kQInv) >= theta) {
@@ -271,13 +271,11 @@ __global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
         sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
         if (S.xin && ed.exchange_every > 0 && ed.R > 1 && (s + 1) % ed.exchange_every == 0) {
             // the exchange round of this ensemble, inside the launch; then the new slot
-            if (lane == 0) S.E[g] = E;
-            if (!ensemble_exchange(S, rd.ens, g, ed.rep_base, ed.R, s + 1, xr, lane)) {
+            if (!ensemble_exchange(S, ed, rd.ens, g, rd.r, E, s + 1, xr, slot, lane)) {
                 if (lane == 0) atomicOr(S.err, kErrTimeout);
                 s_end = s + 1;
                 break;
             }
-            slot = __ldcg(&S.temp_of_rep[g]);  // written by the ensemble's first replica
             gs = rd.slot_base + slot;
             Tf = S.Tf[gs];
         }

@@ -220,14 +220,14 @@ int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonde
 int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, double* out,
                            void* stream);
 
-/* Choose the sweep kernel (creation picks 0 below 24 beads, 4 up to 96, 5 up to 1024, else 2):
+/* Choose the sweep kernel (creation picks 4 up to 40 beads, 5 up to 1024, else 2):
  * 0 = one warp per replica, one move at a time;
  * 1 = one warp per replica, groups of up to 8 consecutive moves with distinct beads
  * evaluated together; 2 = a CTA of 1-8 warps per replica (by N), one move at a time;
  * 3 = a CTA of 2-8 warps per replica, each warp evaluating one move of a group of moves with
  * distinct beads; 4 = one warp per replica with the chain in registers (N_max <= 1024),
  * taking double-float work only where a decision or an accepted dE needs it; 5 = a CTA of
- * 4-8 warps per replica with the chain in every warp's registers, each warp evaluating one
+ * 4, 6 or 8 warps per replica (by N) with the chain in every warp's registers, each warp evaluating one
  * move of a group of consecutive moves on distinct beads, decisions taken in move order
  * (N_max <= 1024). Kernels 0-3 run the same chain, move for move, and differ only in the
  * summation order of dE. Kernels 4 and 5 take each Metropolis decision whose dE lies

@@ -282,10 +282,12 @@ void drop_graph(pt_ctx* h) {
 }
 
 // Kernel choice before any tuning, from timings on GB300 (4 x 64 replicas up to N = 300,
-// 128 replicas above): one warp per replica wins for short chains, the warp-per-move
-// lookahead from about 50 beads on.
+// 128 replicas above; us per sweep, kernels 0 / 4 / 5): N = 10: 16.7 / 15.6 / 18.7;
+// N = 30: 34.6 / 27.9 / 27.9; N = 60: 68.2 / 46.0 / 43.0; N = 1000: kernel 2 945, kernel 5
+// 658. The chain in registers of one warp wins for short chains, a CTA of warps each taking
+// one move of a group from about 40 beads to the register limit, the team kernel beyond.
 int default_variant(int nmax) {
-    return nmax < 24 ? kSweepSimple : nmax <= 96 ? kSweepReg : nmax <= kRegMaxN ? kSweepGrp : kSweepTeam;
+    return nmax <= 40 ? kSweepReg : nmax <= kRegMaxN ? kSweepGrp : kSweepTeam;
 }
 
 pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {

@@ -74,12 +74,15 @@ __host__ __device__ constexpr size_t grp_fixed_bytes() {
     return (size_t)(32 * W) * 2 * sizeof(float4)          // D0, D1
            + (size_t)W * 2 * sizeof(float4)               // GP, GPN
            + (size_t)W * 4 * sizeof(float)                // GL, GH, GV, GFL
-           + (size_t)W * W * 3 * sizeof(float)            // CD, CE, CFL
+           + (size_t)W * W * sizeof(float4)               // CX
            + 16;                                          // first-move decision
 }
 
+// Register cap: two CTAs per SM up to 6 warps and up to 8 warps of <= 8 slots, one otherwise,
+// and no spilling (under a plain launch bound the compiler kept some instantiations to 128
+// registers and spilled).
 template <int U, int W>
-__global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
+__global__ void __maxnreg__(U >= 32 ? 232 : (W >= 8 && U < 16) ? 128 : 168) k_sweep_grp(State S, int chunk) {
     constexpr int T = 32 * W;  // threads, and moves per batch
     extern __shared__ float4 smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -101,10 +104,9 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
     float* GH = GL + W;                       // [W] upper bound
     float* GV = GH + W;                       // [W] value of dE_i (accepted / logged moves)
     unsigned* GFL = reinterpret_cast<unsigned*>(GV + W);  // [W] flags of move i
-    float* CD = reinterpret_cast<float*>(GFL + W);        // [W][W] correction of move i for move l
-    float* CE = CD + W * W;                                // its bound
-    unsigned* CFL = reinterpret_cast<unsigned*>(CE + W * W);  // its flags
-    int* FIRST = reinterpret_cast<int*>(CFL + W * W);     // decision of an undecided first move
+    float4* CX = reinterpret_cast<float4*>(GFL + W);      // [W][W] correction of move i for move l:
+                                                           // value, bound, flags (one load)
+    int* FIRST = reinterpret_cast<int*>(CX + W * W);      // decision of an undecided first move
     float* CW = reinterpret_cast<float*>(FIRST + 4);       // [W][4] per-warp sums of a sweep
     float4* PE = reinterpret_cast<float4*>(CW + 4 * W) + warp * 3 * kPend;  // this warp's pending terms
     int* Q = reinterpret_cast<int*>(reinterpret_cast<float4*>(CW + 4 * W) + W * 3 * kPend);
@@ -263,9 +265,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                         float d, e;
                         unsigned cf;
                         correction_f32(qo, qn, p, pn, kl - k == 1 || k - kl == 1, ljb, d, e, cf);
-                        CD[i * W + l] = d;
-                        CE[i * W + l] = e;
-                        CFL[i * W + l] = cf;
+                        CX[i * W + l] = make_float4(d, e, __uint_as_float(cf), 0.f);
                     }
                     if (lane == 0) {
                         GP[i] = make_float4(p.x, p.y, p.z, __int_as_float(k));
@@ -280,21 +280,68 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                 unsigned amask = 0u;
                 int nd = w;
                 {
+                    // only the lanes of group moves read (every warp of the CTA and of its
+                    // neighbour CTAs on the SM does this at once: shared-memory wavefronts count)
                     const bool mine = lane < w;
-                    const float lo0 = mine ? GL[lane] : kNaN, hi0 = mine ? GH[lane] : kNaN;
-                    const float th = mine ? D1[g0 + lane].x : 0.f;
+                    float lo0 = kNaN, hi0 = kNaN, th = 0.f;
                     float cd[W], ce[W];
                     unsigned cf[W];
 #pragma unroll
                     for (int l = 0; l < W; ++l) {
-                        const bool has = mine && l < lane;
-                        cd[l] = has ? CD[lane * W + l] : 0.f;
-                        ce[l] = has ? CE[lane * W + l] : 0.f;
-                        cf[l] = has ? CFL[lane * W + l] : 0u;
+                        cd[l] = ce[l] = 0.f;
+                        cf[l] = 0u;
+                    }
+                    if (mine) {
+                        lo0 = GL[lane];
+                        hi0 = GH[lane];
+                        th = D1[g0 + lane].x;
+#pragma unroll
+                        for (int l = 0; l < W; ++l) {
+                            if (l < lane) {
+                                const float4 c = CX[lane * W + l];
+                                cd[l] = c.x;
+                                ce[l] = c.y;
+                                cf[l] = __float_as_uint(c.z);
+                            }
+                        }
+                    }
+                    // Fast path: every move's interval widened to cover any subset of the earlier
+                    // moves being accepted. Where all of them decide, the decisions are the ones
+                    // taken in order; the group then ends at the first move whose value would
+                    // rest on an inexact correction of an accepted earlier move.
+                    float rlo = lo0, rhi = hi0;
+                    bool rok_lo = lo0 == lo0, rok_hi = hi0 == hi0;
+#pragma unroll
+                    for (int l = 0; l < W; ++l) {
+                        if (mine && l < lane) {
+                            if ((cf[l] & 2u) || cd[l] != cd[l]) {
+                                rok_lo = rok_hi = false;
+                            } else {
+                                rlo = __fadd_rd(rlo, fminf(__fsub_rd(cd[l], ce[l]), 0.f));
+                                rhi = __fadd_ru(rhi, fmaxf(__fadd_ru(cd[l], ce[l]), 0.f));
+                            }
+                        }
+                    }
+                    int rdec = 2;
+                    if (mine && rok_lo && rlo >= th) rdec = 0;
+                    else if (mine && rok_hi && rhi < th) rdec = 1;
+                    const unsigned wm = (1u << w) - 1u;
+                    const bool all_known = (__ballot_sync(kFull, rdec != 2) & wm) == wm;
+                    if (all_known) {
+                        amask = __ballot_sync(kFull, rdec == 1) & wm;
+                        bool cin = false;
+#pragma unroll
+                        for (int l = 0; l < W; ++l)
+                            if (mine && l < lane && ((amask >> l) & 1u)) cin |= cf[l] != 0u;
+                        const unsigned tb = __ballot_sync(kFull, cin && (rdec == 1 || logging)) & wm;
+                        if (tb) {
+                            nd = __ffs(tb) - 1;
+                            amask &= (1u << nd) - 1u;
+                        }
                     }
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
-                        if (i >= w) break;
+                        if (all_known || i >= w) break;
                         // every lane forms its own interval under the decisions so far; lane i's counts
                         float lo = lo0, hi = hi0;
                         bool ok_lo = lo0 == lo0, ok_hi = hi0 == hi0, cin = false;
@@ -464,7 +511,7 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
                             v = warp_sum(part);
                         }
                         for (int l = 0; l < i; ++l)
-                            if ((amask >> l) & 1u) v = __fadd_rn(v, CD[i * W + l]);
+                            if ((amask >> l) & 1u) v = __fadd_rn(v, CX[i * W + l].x);
                     }
                     if (acc_i) {
                         wdsum = df_add(wdsum, df{v, 0.f});
@@ -538,10 +585,13 @@ __global__ void __launch_bounds__(32 * W) k_sweep_grp(State S, int chunk) {
     }
 }
 
-int grp_warps(int nmax) { return nmax <= 200 ? 4 : 8; }
+// Warps per CTA (the longest group): from timings on GB300 at 64 replicas x 4 ensembles up to
+// N = 300 and 128 replicas above (us per sweep, W = 4 / 6 / 8): N = 30: 28.2 / 29.4 / 32.4;
+// N = 100: 66.4 / 63.7 / 68.1; N = 300: 206.9 / 200.9 / -; N = 1000: 968 / 746 / 654.
+int grp_warps(int nmax) { return nmax < 48 ? 4 : nmax <= 300 ? 6 : 8; }
 
 size_t grp_smem_bytes(int nmax, int warps) {
-    const size_t fixed = warps == 4 ? grp_fixed_bytes<4>() : grp_fixed_bytes<8>();
+    const size_t fixed = warps == 4 ? grp_fixed_bytes<4>() : warps == 6 ? grp_fixed_bytes<6>() : grp_fixed_bytes<8>();
     return (size_t)nmax * sizeof(float4) + fixed + 4 * sizeof(float) * warps +
            (size_t)warps * 3 * kPend * sizeof(float4) + (size_t)warps * nmax * sizeof(int) + (size_t)nmax + 16;
 }
@@ -616,26 +666,28 @@ static bool fits_grp_w(int n_blocks, int nmax, size_t smem, int num_sms) {
 bool grp_coop_fits(const State& s, int nmax, int num_sms) {
     const int w = grp_warps(nmax);
     const size_t smem = grp_smem_bytes(nmax, w);
-    return w == 4 ? fits_grp_w<4>(s.n_reps, nmax, smem, num_sms) : fits_grp_w<8>(s.n_reps, nmax, smem, num_sms);
+    return w == 4   ? fits_grp_w<4>(s.n_reps, nmax, smem, num_sms)
+           : w == 6 ? fits_grp_w<6>(s.n_reps, nmax, smem, num_sms)
+                    : fits_grp_w<8>(s.n_reps, nmax, smem, num_sms);
 }
 
 cudaError_t launch_sweep_grp_coop(const State& s, int chunk, cudaStream_t st) {
     const int w = grp_warps(s.nmax);
     const size_t smem = grp_smem_bytes(s.nmax, w);
-    return w == 4 ? coop_grp_w<4>(s, chunk, st, smem) : coop_grp_w<8>(s, chunk, st, smem);
+    return w == 4 ? coop_grp_w<4>(s, chunk, st, smem) : w == 6 ? coop_grp_w<6>(s, chunk, st, smem) : coop_grp_w<8>(s, chunk, st, smem);
 }
 
 cudaError_t configure_sweep_grp(int nmax) {
     const int w = grp_warps(nmax);
     const size_t smem = grp_smem_bytes(nmax, w);
     if (smem <= 48 * 1024) return cudaSuccess;
-    return w == 4 ? configure_grp_w<4>((int)smem) : configure_grp_w<8>((int)smem);
+    return w == 4 ? configure_grp_w<4>((int)smem) : w == 6 ? configure_grp_w<6>((int)smem) : configure_grp_w<8>((int)smem);
 }
 
 cudaError_t launch_sweep_grp(const State& s, int chunk, cudaStream_t st) {
     const int w = grp_warps(s.nmax);
     const size_t smem = grp_smem_bytes(s.nmax, w);
-    return w == 4 ? launch_grp_w<4>(s, chunk, st, smem) : launch_grp_w<8>(s, chunk, st, smem);
+    return w == 4 ? launch_grp_w<4>(s, chunk, st, smem) : w == 6 ? launch_grp_w<6>(s, chunk, st, smem) : launch_grp_w<8>(s, chunk, st, smem);
 }
 
 }  // namespace ptgb

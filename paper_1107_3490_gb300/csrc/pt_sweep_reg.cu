@@ -30,8 +30,10 @@
 
 namespace ptgb {
 
+// Register cap: enough for the chain slots and the move without spilling (with a launch
+// bound of 32 threads the compiler kept to 128 registers and ran slightly slower).
 template <int U>
-__global__ void __launch_bounds__(32) k_sweep_reg(State S, int chunk) {
+__global__ void __maxnreg__(U >= 32 ? 248 : 168) k_sweep_reg(State S, int chunk) {
     extern __shared__ float4 smem[];
     const int lane = threadIdx.x;
     const int g = blockIdx.x;

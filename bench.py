@@ -418,7 +418,7 @@ def run_served(args):
             "data": "synthetic", "dtype": "f32",
             "config": {"workload": f"{n_jobs} PT jobs, Poisson arrivals {args.rate}/s, N log-uniform 20-1000, "
                                    "replicas uniform 16-128, budgets log-uniform 100-1000 sweeps, exchange every "
-                                   "sweep; server N_max 1000", "sweep_kernel": "k_sweep_team (the server default)"},
+                                   "sweep; server N_max 1000", "sweep_kernel": KERNEL_NAMES[args.kernel] if args.kernel >= 0 else "k_sweep_team (the server default)"},
             "latency_s": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                           "max": lat[-1]},
             "makespan_s": makespan,

@@ -252,9 +252,10 @@ int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen);
 /* Launch mode. 1 (default): with kernel 4 or 5, when every replica's block can be resident
  * at once, a pt_sweep call with exchange_every >= 1 is one cooperative launch that runs all
  * its sweeps, each ensemble's exchange rounds done inside the kernel: the replicas of an
- * ensemble meet at a device barrier after the sweep an exchange follows, the ensemble's
- * first replica runs the round (Eq. 6) and releases the others. Every wait is bounded (about
- * a second); a wait that gives up makes the call's later checks return PT_ETIMEOUT. 0: one
+ * ensemble meet at a device barrier after the sweep an exchange follows (each publishing its
+ * energy under its temperature slot) and every replica then decides its own pair of the
+ * round (Eq. 6). Every wait is bounded (seconds); a wait that gives up makes the call's later
+ * checks return PT_ETIMEOUT. 0: one
  * launch per sweep (replayed from a CUDA graph) and a separate exchange kernel. Both modes
  * run the same chain. pt_get_launch_mode returns the mode pt_sweep will actually use. */
 int pt_set_launch_mode(pt_ctx* h, int mode);

@@ -220,7 +220,8 @@ int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonde
 int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, double* out,
                            void* stream);
 
-/* Choose the sweep kernel (creation picks 4 up to 40 beads, 5 up to 1024, else 2):
+/* Choose the sweep kernel (creation picks 4 up to 40 beads, 5 up to 1024 (4 up to 300 beads
+ * when kernel 5's CTAs for every replica do not fit on the GPU at once), else 2):
  * 0 = one warp per replica, one move at a time;
  * 1 = one warp per replica, groups of up to 8 consecutive moves with distinct beads
  * evaluated together; 2 = a CTA of 1-8 warps per replica (by N), one move at a time;

@@ -458,15 +458,26 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
         if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) h->gpu_name = prop.name;
     }
     h->variant = default_variant(h->nmax);
-    h->warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, h->variant);
-    ce = configure_sweep(h->nmax, h->warps, h->variant);
-    if (ce != cudaSuccess) {
-        cudaGetLastError();
-        fail(PT_ECUDA, "configure sweep kernel: %s", cudaGetErrorString(ce));
-        pt_destroy(h);
-        return nullptr;
+    for (;;) {
+        h->warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, h->variant);
+        ce = configure_sweep(h->nmax, h->warps, h->variant);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            fail(PT_ECUDA, "configure sweep kernel: %s", cudaGetErrorString(ce));
+            pt_destroy(h);
+            return nullptr;
+        }
+        h->coop_ok = sweep_coop_fits(h->S, h->nmax, h->variant, h->num_sms);
+        // More replicas than kernel 5's CTAs that fit on the GPU at once: up to 300 beads one
+        // warp per replica (kernel 4) does the same work in fewer instructions, and with every
+        // replica resident (N = 55, 960 replicas, the paper's protocol: 47 against 122 us per
+        // sweep).
+        if (h->variant == kSweepGrp && !h->coop_ok && h->nmax <= 300) {
+            h->variant = kSweepReg;
+            continue;
+        }
+        break;
     }
-    h->coop_ok = sweep_coop_fits(h->S, h->nmax, h->variant, h->num_sms);
     return h;
 }
 

@@ -262,6 +262,13 @@ int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen);
 int pt_set_launch_mode(pt_ctx* h, int mode);
 int pt_get_launch_mode(const pt_ctx* h);
 
+/* Failure-path test: lowers ensemble e's count of arrivals at the in-kernel exchange barrier
+ * by one, so that the next exchange round of a persistent launch can never complete. Every
+ * replica's bounded wait then gives up (after about a second), the launch ends and the next
+ * call that checks returns PT_ETIMEOUT (once). The context stays usable; pt_restore of a
+ * checkpoint resets the barrier. PT_EINVAL before the ensemble's first exchange round. */
+int pt_test_stall_exchange(pt_ctx* h, int ensemble);
+
 /* Kernel timing for profiling: with on = 1 every sweep-kernel launch is bracketed by CUDA
  * events on the context's stream (inside the captured graph too). pt_kernel_timing then
  * reports the mean sweep-kernel time per sweep over the launches that did work in the most

@@ -214,7 +214,13 @@ int sync_and_check(pt_ctx* h) {
         h->poisoned = PT_ESTATE;
         return fail(PT_ESTATE, "non-finite energy found on the device");
     }
-    if (err & kErrTimeout) return fail(PT_ETIMEOUT, "a bounded device wait gave up");
+    if (err & kErrTimeout) {
+        // reported once: the replicas stopped at the sweep where the wait gave up; the caller
+        // restores a checkpoint (which also resets the exchange barrier) and carries on
+        const int keep = err & ~kErrTimeout;
+        CK(h, cudaMemcpy(h->S.err, &keep, sizeof(int), cudaMemcpyHostToDevice));
+        return fail(PT_ETIMEOUT, "a bounded device wait gave up");
+    }
     return PT_OK;
 }
 
@@ -687,6 +693,19 @@ extern "C" int pt_set_sweep_kernel(pt_ctx* h, int variant) {
     h->warps = warps;
     h->coop_ok = sweep_coop_fits(h->S, h->nmax, variant, h->num_sms);
     drop_graph(h);
+    return PT_OK;
+}
+
+extern "C" int pt_test_stall_exchange(pt_ctx* h, int ensemble) {
+    int rc = check_usable(h);
+    if (rc) return rc;
+    if (ensemble < 0 || ensemble >= (int)h->ens.size()) return fail(PT_EINVAL, "no ensemble %d", ensemble);
+    if ((rc = sync_and_check(h))) return rc;
+    unsigned long long a = 0;
+    CK(h, cudaMemcpy(&a, h->S.xarrive + ensemble, sizeof a, cudaMemcpyDeviceToHost));
+    if (a == 0) return fail(PT_EINVAL, "pt_test_stall_exchange: run one exchange round first");
+    --a;
+    CK(h, cudaMemcpy(h->S.xarrive + ensemble, &a, sizeof a, cudaMemcpyHostToDevice));
     return PT_OK;
 }
 

@@ -135,8 +135,9 @@ __device__ __forceinline__ void exchange_round_warp(const State& S, int e, int64
 }
 
 // Bounded wait (lane 0 polls, the warp waits) until *p >= target; false if it gave up. A
-// poll costs an L2 round trip plus 32 ns, so the limit is seconds, far above one sweep.
-constexpr long long kWaitPolls = 1ll << 23;
+// poll costs an L2 round trip plus 32 ns, so the limit is about a second, far above the
+// longest sweep a persistent launch runs (N = 1024 with its periodic FP64 recompute: ~15 ms).
+constexpr long long kWaitPolls = 1ll << 21;
 __device__ __forceinline__ bool wait_at_least(unsigned long long* p, unsigned long long target, int lane) {
     int ok = 1;
     if (lane == 0) {

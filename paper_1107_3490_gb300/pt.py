@@ -82,6 +82,7 @@ _SIGS = {
     "pt_set_sweep_kernel": (_I, [_V, _I]),
     "pt_set_launch_mode": (_I, [_V, _I]),
     "pt_get_launch_mode": (_I, [_V]),
+    "pt_test_stall_exchange": (_I, [_V, _I]),
     "pt_get_sweep_kernel": (_I, [_V]),
     "pt_autotune": (_I, [_V, _I, _I, ctypes.POINTER(ctypes.c_int)]),
     "pt_set_kernel_timing": (_I, [_V, _I]),
@@ -362,6 +363,11 @@ def pt_set_launch_mode(h, mode: int) -> None:
 
 def pt_get_launch_mode(h) -> int:
     return lib().pt_get_launch_mode(h)
+
+
+def pt_test_stall_exchange(h, ensemble: int) -> None:
+    """Failure-path test: the ensemble's next in-kernel exchange barrier cannot complete."""
+    _ck(lib().pt_test_stall_exchange(h, int(ensemble)))
 
 
 def pt_get_sweep_kernel(h) -> int:

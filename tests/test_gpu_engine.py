@@ -356,3 +356,35 @@ def test_fp32_fma_rate_is_near_the_derived_peak():
     assert derived / 3 < tflops < derived, (tflops, derived)
     with pytest.raises(pt.PtError):
         pt.pt_fp32_fma_rate(0, 0)
+
+
+@pytest.mark.parametrize("variant", [4, 5])
+def test_exchange_barrier_wait_gives_up_and_the_context_recovers(variant):
+    """A stalled in-kernel exchange barrier (one arrival short, made on the host): every
+    replica's bounded wait gives up, the call reports PT_ETIMEOUT once, and after a restore the
+    chain continues exactly as an undisturbed one."""
+    import time
+    ref, h = _make(N=60, R=6, seed=31), _make(N=60, R=6, seed=31)
+    try:
+        for x in (ref, h):
+            pt.pt_set_sweep_kernel(x, variant)
+            pt.pt_set_launch_mode(x, 1)
+        assert pt.pt_get_launch_mode(h) == 1
+        pt.pt_sweep(h, 7, 1)
+        host = np.zeros(pt.pt_checkpoint_size(h), dtype=np.uint8)
+        n = pt.pt_checkpoint_into(h, host)
+        pt.pt_test_stall_exchange(h, 0)
+        t0 = time.time()
+        pt.pt_sweep(h, 10, 1)
+        with pytest.raises(pt.PtError) as err:
+            pt.pt_sync(h)
+        assert err.value.code == pt.PT_ETIMEOUT
+        assert time.time() - t0 < 30
+        pt.pt_sync(h)  # reported once
+        pt.pt_restore_from(h, host, n)
+        pt.pt_sweep(h, 10, 1)
+        pt.pt_sweep(ref, 17, 1)
+        _same(_state(h), _state(ref))
+    finally:
+        pt.pt_destroy(h)
+        pt.pt_destroy(ref)

@@ -220,6 +220,16 @@ __global__ void __maxnreg__(U >= 32 ? 232 : (W >= 8 && U < 16) ? 128 : 168) k_sw
                     p = make_float3(p4.x, p4.y, p4.z);
                     pn = make_float3(__fadd_rn(p.x, __fmul_rn(delta, d0.y)), __fadd_rn(p.y, __fmul_rn(delta, d0.z)),
                                      __fadd_rn(p.z, __fmul_rn(delta, d0.w)));
+                    // the LJ corrections for earlier group moves (lane l < i; the other lanes
+                    // take a stand-in), branch-free so that they interleave with the row
+                    const int lc = lane < i ? lane : 0;
+                    const float4 e0 = D0[g0 + lc];
+                    const int kl = __float_as_int(e0.x) & 0xffff;
+                    const float4 qo = P[kl];
+                    const float4 qn = make_float4(__fadd_rn(qo.x, __fmul_rn(delta, e0.y)),
+                                                  __fadd_rn(qo.y, __fmul_rn(delta, e0.z)),
+                                                  __fadd_rn(qo.z, __fmul_rn(delta, e0.w)), 0.f);
+                    const PairF ca = lj_pair_f32(qn, p, pn), cb = lj_pair_f32(qo, p, pn);
                     const RowSums rs = row_pass<U>(qx, qy, qz, p, pn, k, lane, N);
                     aord = rs.aord;
                     stm = rs.stm;
@@ -253,19 +263,19 @@ __global__ void __maxnreg__(U >= 32 ? 232 : (W >= 8 && U < 16) ? 128 : 168) k_sw
                     const int sh = __reduce_add_sync(kFull, qh);
                     mfl = __reduce_or_sync(kFull, (lo_bad ? 1u : 0u) | (hi_bad ? 2u : 0u) | (rs.stm ? 4u : 0u) |
                                                       ((bf & 7u) ? 8u : 0u));
-                    // corrections for accepted earlier group moves: lane l < i
+                    // corrections for accepted earlier group moves, lane l < i: the LJ ones from
+                    // beside the row, the bonded ones here
                     if (lane < i) {
-                        const int l = lane;
-                        const float4 e0 = D0[g0 + l];
-                        const int kl = __float_as_int(e0.x) & 0xffff;
-                        const float4 qo = P[kl];
-                        const float4 qn = make_float4(__fadd_rn(qo.x, __fmul_rn(delta, e0.y)),
-                                                      __fadd_rn(qo.y, __fmul_rn(delta, e0.z)),
-                                                      __fadd_rn(qo.z, __fmul_rn(delta, e0.w)), 0.f);
                         float d, e;
                         unsigned cf;
-                        correction_f32(qo, qn, p, pn, kl - k == 1 || k - kl == 1, ljb, d, e, cf);
-                        CX[i * W + l] = make_float4(d, e, __uint_as_float(cf), 0.f);
+                        if (kl - k == 1 || k - kl == 1) {
+                            correction_f32(qo, qn, p, pn, true, ljb, d, e, cf);
+                        } else {
+                            cf = (ca.steep || cb.steep) ? 1u : 0u;
+                            d = __fsub_rn(ca.t, cb.t);
+                            e = __fadd_ru(__fadd_ru(ca.e, cb.e), 2.f * kEps0 * fabsf(d));
+                        }
+                        CX[i * W + lane] = make_float4(d, e, __uint_as_float(cf), 0.f);
                     }
                     if (lane == 0) {
                         GP[i] = make_float4(p.x, p.y, p.z, __int_as_float(k));

@@ -178,6 +178,22 @@ static __device__ __noinline__ float move_value_accurate(const float4* P, int* Q
     return v;
 }
 
+// Inclusive prefix over the lanes of a count 0 <= cnt <= U, and the total: one ballot per bit
+// of cnt, so no chain of shuffles.
+template <int U>
+__device__ __forceinline__ void lane_offsets(int cnt, int lane, int& pre, int& tot) {
+    constexpr int kBits = U >= 32 ? 6 : U >= 16 ? 5 : U >= 8 ? 4 : U >= 4 ? 3 : U >= 2 ? 2 : 1;
+    const unsigned le = 0xffffffffu >> (31 - lane);  // lanes <= this one
+    pre = 0;
+    tot = 0;
+#pragma unroll
+    for (int b = 0; b < kBits; ++b) {
+        const unsigned m = __ballot_sync(0xffffffffu, (cnt >> b) & 1);
+        pre += __popc(m & le) << b;
+        tot += __popc(m) << b;
+    }
+}
+
 // Deferred accurate terms. An accepted move whose dE the decision did not need exactly
 // enters the energy with its FP32 value; each of its inexact terms (a steep pair, a bond far
 // from r0) is recorded with the positions it was evaluated at, and later the warp adds

@@ -457,13 +457,9 @@ __global__ void __maxnreg__(U >= 32 ? 232 : (W >= 8 && U < 16) ? 128 : 168) k_sw
                             // the group) at the end of the sweep
                             v = warp_sum(part);
                             const int cnt = __popc(stm);
-                            int pre = cnt;
-#pragma unroll
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const int y = __shfl_up_sync(kFull, pre, o);
-                                if (lane >= o) pre += y;
-                            }
-                            const int tot = __shfl_sync(kFull, pre, 31) + ((mfl & 8u) ? 2 : 0);
+                            int pre, tot;
+                            lane_offsets<U>(cnt, lane, pre, tot);
+                            tot += (mfl & 8u) ? 2 : 0;
                             if (npend + tot > kPend) {
                                 cw = __fadd_rn(cw, pending_correction(PE, npend, lane));
                                 npend = 0;

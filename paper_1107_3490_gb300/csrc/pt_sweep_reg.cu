@@ -200,13 +200,9 @@ __global__ void __maxnreg__(U >= 32 ? 248 : 168) k_sweep_reg(State S, int chunk)
                             // a certain acceptance: its FP32 dE now, the accurate remainder of
                             // its steep pairs and bonds later (pending_correction)
                             const int cnt = __popc(rs.stm);
-                            int pre = cnt;
-#pragma unroll
-                            for (int o = 1; o < 32; o <<= 1) {
-                                const int y = __shfl_up_sync(kFull, pre, o);
-                                if (lane >= o) pre += y;
-                            }
-                            const int tot = __shfl_sync(kFull, pre, 31) + ((fl & 8u) ? 2 : 0);
+                            int pre, tot;
+                            lane_offsets<U>(cnt, lane, pre, tot);
+                            tot += (fl & 8u) ? 2 : 0;
                             if (npend + tot > kPend) {
                                 const float c = pending_correction(PE, npend, lane);
                                 dsum = df_add(dsum, df{c, 0.f});

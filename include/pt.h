@@ -138,8 +138,9 @@ int pt_moments(pt_ctx* h, double* out, int64_t n);
  * their centre of mass), of r_gyr^4, of R_ee^2 (squared end-to-end distance), of R_ee^4, of
  * E r_gyr^2 and of E R_ee^2; [slot][6] FP64, n == 6 x slots. With the measurement count of
  * pt_moments these give <r_gyr^2>, its variance, and the fluctuation
- * d<r_gyr^2>/dT = beta^2 (<E r_gyr^2> - <E><r_gyr^2>). Computed in FP64 from the float
- * coordinates, so they equal an FP64 evaluation up to summation order. */
+ * d<r_gyr^2>/dT = beta^2 (<E r_gyr^2> - <E><r_gyr^2>). Each sweep's r_gyr^2 and R_ee^2 are
+ * computed in double-float arithmetic from the float coordinates (about 1e-13 relative to an
+ * FP64 evaluation) and accumulated in FP64. */
 int pt_observables(pt_ctx* h, double* out, int64_t n);
 
 /* Per temperature slot and energy bin (the layout of pt_histograms): the sums of r_gyr^2 and

@@ -71,8 +71,9 @@ def _full_match(rep, out, orc, S):
     assert np.abs(out["hist"] - orc.hist).sum() <= 2
     np.testing.assert_allclose(out["mom"][:, 0], orc.mom[:, 0], rtol=0, atol=0)
     np.testing.assert_allclose(out["mom"][:, 1], orc.mom[:, 1], rtol=1e-9, atol=S * rep.max_e_err + 1e-9)
-    # shape observables (Sec. 4.1): FP64 on both sides from the same float coordinates, so
-    # they agree up to summation order; the E-weighted sums carry the energy tolerance
+    # shape observables (Sec. 4.1) from the same float coordinates: double-float on the
+    # device (about 1e-13 relative), FP64 in the oracle; the E-weighted sums carry the energy
+    # tolerance
     np.testing.assert_allclose(out["obs"][:, :4], orc.obs[:, :4], rtol=1e-12, atol=0)
     scale = np.max(np.abs(orc.obs[:, [0, 2]]), axis=1) + 1e-30
     for c in (4, 5):

@@ -286,9 +286,9 @@ def run_gpu(args):
     roofline["peak_measured_fma"] = fma_tflops
     roofline["frac_of_measured_fma"] = achieved / fma_tflops
 
-    # every step: the target-setting launch, then one cooperative launch (persistent mode)
-    # or graphs of 32 (sweep, exchange) launch pairs
-    launches_per_step = 2 if lmode == 1 else 1 + -(-SWEEPS_PER_STEP // 32) * 64
+    # every step: the target-setting launch, then one cooperative launch and the round-count
+    # update (persistent mode) or graphs of 32 (sweep, exchange) launch pairs
+    launches_per_step = 3 if lmode == 1 else 1 + -(-SWEEPS_PER_STEP // 32) * 64
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -254,20 +254,20 @@ int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen);
 /* Launch mode. 1 (default): with kernel 4 or 5, when every replica's block can be resident
  * at once, a pt_sweep call with exchange_every >= 1 is one cooperative launch that runs all
  * its sweeps, each ensemble's exchange rounds done inside the kernel: the replicas of an
- * ensemble meet at a device barrier after the sweep an exchange follows (each publishing its
- * energy under its temperature slot) and every replica then decides its own pair of the
- * round (Eq. 6). Every wait is bounded (seconds); a wait that gives up makes the call's later
- * checks return PT_ETIMEOUT. 0: one
+ * ensemble publish their energies under their temperature slots after the sweep an exchange
+ * follows, and each replica waits for its partner of the round alone and takes its pair's
+ * decision (Eq. 6). Every wait is bounded (about half a second); a wait that gives up makes
+ * the call's later checks return PT_ETIMEOUT. 0: one
  * launch per sweep (replayed from a CUDA graph) and a separate exchange kernel. Both modes
  * run the same chain. pt_get_launch_mode returns the mode pt_sweep will actually use. */
 int pt_set_launch_mode(pt_ctx* h, int mode);
 int pt_get_launch_mode(const pt_ctx* h);
 
-/* Failure-path test: lowers ensemble e's count of arrivals at the in-kernel exchange barrier
- * by one, so that the next exchange round of a persistent launch can never complete. Every
- * replica's bounded wait then gives up (after about a second), the launch ends and the next
- * call that checks returns PT_ETIMEOUT (once). The context stays usable; pt_restore of a
- * checkpoint resets the barrier. PT_EINVAL before the ensemble's first exchange round. */
+/* Failure-path test: raises by one the round every replica of ensemble e waits for from its
+ * exchange partner inside a persistent launch, so that no round of that ensemble can complete.
+ * Every paired replica's bounded wait then gives up (after about half a second), the launch
+ * ends and the next call that checks returns PT_ETIMEOUT (once). The context stays usable;
+ * pt_restore of a checkpoint clears the hold and the exchange state. */
 int pt_test_stall_exchange(pt_ctx* h, int ensemble);
 
 /* Kernel timing for profiling: with on = 1 every sweep-kernel launch is bracketed by CUDA

@@ -196,7 +196,7 @@ void free_state(pt_ctx* h) {
     State& S = h->S;
     void* ptrs[] = {S.reps, S.ens, S.pos, S.E, S.temp_of_rep, S.rep_of_temp, S.Tf, S.beta, S.hist,
                     S.outl, S.mom, S.obs, S.obs_rg2_hist, S.obs_ree2_hist, S.mv_att, S.mv_acc, S.ex_att,
-                    S.ex_acc, S.drift, S.rep_sweep, S.err, S.xarrive, S.xE, S.log_bead, S.log_de, S.log_theta, S.log_acc,
+                    S.ex_acc, S.drift, S.rep_sweep, S.err, S.xstamp, S.xE, S.xhold, S.xrep, S.log_bead, S.log_de, S.log_theta, S.log_acc,
                     S.log_e, S.log_x, h->scratch, h->conf_buf, h->eout_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -387,8 +387,10 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     A(dalloc(&S.drift, G));
     A(dalloc(&S.rep_sweep, G));
     A(dalloc(&S.err, 1));
-    A(dalloc(&S.xarrive, (size_t)n_ens));
-    A(dalloc(&S.xE, 2 * G));
+    A(dalloc(&S.xstamp, G));
+    A(dalloc(&S.xE, 4 * G));
+    A(dalloc(&S.xhold, (size_t)n_ens));
+    A(dalloc(&S.xrep, 2 * G));
     if (a != cudaSuccess) {
         fail(a == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA, "device allocation: %s", cudaGetErrorString(a));
         pt_destroy(h);
@@ -598,6 +600,15 @@ int pt_ensemble_shape(const pt_ctx* h, int e, int* N, int* n_replicas, int* n_bi
 }  // extern "C"
 
 namespace {
+__global__ void k_rounds_from_replicas(EnsDev* ens, int n_ens, const int64_t* xrep, int G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n_ens) {
+        const int b = ens[e].rep_base;
+        ens[e].xround = xrep[b];
+        ens[e].last_x_sweep = xrep[G + b];
+    }
+}
+
 __global__ void k_set_targets(EnsDev* ens, int n_ens, int64_t add, int xe) {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n_ens) {
@@ -643,8 +654,14 @@ extern "C" int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every) {
             h->t_count = 0;
             h->t_next = 0;
         }
-        for (int64_t left = n_sweeps; left > 0; left -= kMaxPersistent)
+        for (int64_t left = n_sweeps; left > 0; left -= kMaxPersistent) {
             CK(h, timed_sweep(h, (int)std::min<int64_t>(left, kMaxPersistent), true));
+            // the replicas' round counts into the ensembles (no block may change what the
+            // others read at their start, so this follows the launch)
+            k_rounds_from_replicas<<<(int)((h->ens.size() + 127) / 128), 128, 0, h->stream>>>(
+                h->S.ens, (int)h->ens.size(), h->S.xrep, h->G);
+            CK(h, cudaGetLastError());
+        }
     } else if (xe == 1) {
         if (!h->graph1 && (rc = build_graph1(h))) return rc;
         // repeated launches past the target do nothing: sweeps stop at the target and the
@@ -701,11 +718,8 @@ extern "C" int pt_test_stall_exchange(pt_ctx* h, int ensemble) {
     if (rc) return rc;
     if (ensemble < 0 || ensemble >= (int)h->ens.size()) return fail(PT_EINVAL, "no ensemble %d", ensemble);
     if ((rc = sync_and_check(h))) return rc;
-    unsigned long long a = 0;
-    CK(h, cudaMemcpy(&a, h->S.xarrive + ensemble, sizeof a, cudaMemcpyDeviceToHost));
-    if (a == 0) return fail(PT_EINVAL, "pt_test_stall_exchange: run one exchange round first");
-    --a;
-    CK(h, cudaMemcpy(h->S.xarrive + ensemble, &a, sizeof a, cudaMemcpyHostToDevice));
+    const int one = 1;
+    CK(h, cudaMemcpy(h->S.xhold + ensemble, &one, sizeof one, cudaMemcpyHostToDevice));
     return PT_OK;
 }
 
@@ -1140,10 +1154,9 @@ extern "C" int pt_restore(pt_ctx* h, const void* buf, size_t size) {
         CK(h, cudaMemcpy(b.dev, p, b.bytes, cudaMemcpyHostToDevice));
         p += b.bytes;
     }
-    // the in-kernel exchange barrier counts R arrivals per round
-    std::vector<unsigned long long> arr(eds.size());
-    for (size_t e = 0; e < eds.size(); ++e) arr[e] = (unsigned long long)eds[e].xround * (unsigned long long)eds[e].R;
-    CK(h, cudaMemcpy(h->S.xarrive, arr.data(), arr.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+    // the in-kernel exchange: no published round ahead of the restored one, no hold
+    CK(h, cudaMemset(h->S.xstamp, 0, sizeof(unsigned long long) * (size_t)h->G));
+    CK(h, cudaMemset(h->S.xhold, 0, sizeof(int) * h->ens.size()));
     h->done = (int64_t)hdr[2];
     return PT_OK;
 }

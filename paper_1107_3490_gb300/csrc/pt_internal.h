@@ -54,11 +54,13 @@ struct State {
     double* drift;            // [replica]
     int64_t* rep_sweep;       // [replica] sweeps done
     int* err;                 // error bits
-    // in-kernel exchange of persistent launches: per ensemble, arrivals at the ensemble
-    // barrier (R per round); energies published by slot, two buffers by round parity
-    // ([2][replica]); xin != 0 in such a launch
-    unsigned long long* xarrive;
+    // in-kernel exchange of persistent launches (xin != 0): per global slot, the round + 1 of
+    // the latest energy published there (xstamp) and the energies, four buffers by round
+    // ([4][slot], xE); per ensemble, a hold added to every wait target (0; a test sets 1)
+    unsigned long long* xstamp;
     double* xE;
+    int* xhold;
+    int64_t* xrep;  // [2][replica]: rounds done and sweep of the last round, at launch end
     int xin;
     // per-move log of sweeps [log_s0, log_s0 + log_ns); null pointers when off
     int64_t log_s0, log_ns, log_pstride;  // log_pstride = total positions

@@ -848,8 +848,7 @@ __global__ void __launch_bounds__(NW * 32) k_sweep_wpm(State S, int chunk) {
     }
 }
 
-// One exchange round per ensemble that is due (Sec. 3.3, Eq. 6): one warp per ensemble. It
-// also keeps the in-kernel barrier's counter at R arrivals per round.
+// One exchange round per ensemble that is due (Sec. 3.3, Eq. 6): one warp per ensemble.
 __global__ void k_exchange(State S) {
     const int lane = threadIdx.x & 31;
     const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -860,7 +859,6 @@ __global__ void k_exchange(State S) {
     const int xe = ed->exchange_every;
     if (xe <= 0 || R < 2 || sw == 0 || sw % xe != 0 || sw <= ed->last_x_sweep) return;
     exchange_round_warp(S, e, sw, lane);
-    if (lane == 0 && S.xarrive) S.xarrive[e] += (unsigned long long)R;
 }
 
 // Row chunks per conformation: a function of N alone, so that a conformation's FP64 sum

@@ -134,48 +134,28 @@ __device__ __forceinline__ void exchange_round_warp(const State& S, int e, int64
     }
 }
 
-// Bounded wait (lane 0 polls, the warp waits) until *p >= target; false if it gave up. A
-// poll costs an L2 round trip plus 32 ns, so the limit is about a second, far above the
-// longest sweep a persistent launch runs (N = 1024 with its periodic FP64 recompute: ~15 ms).
+// Polls of a bounded in-kernel wait. A poll costs an L2 round trip plus 32 ns, so the limit
+// is about half a second, far above the longest sweep a persistent launch runs (N = 1024 with
+// its periodic FP64 recompute: ~15 ms).
 constexpr long long kWaitPolls = 1ll << 21;
-__device__ __forceinline__ bool wait_at_least(unsigned long long* p, unsigned long long target, int lane) {
-    int ok = 1;
-    if (lane == 0) {
-        long long it = 0;
-        while (*(volatile unsigned long long*)p < target) {
-            if (++it > kWaitPolls) {
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-    }
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
 
 // In-kernel exchange after sweep count sw (persistent launches; one warp of every replica of
-// ensemble e calls it, lane 0 does the work). The replica publishes its energy under its
-// temperature slot in the round's buffer (xE, two buffers by round parity), arrives at the
-// ensemble barrier (R arrivals per round) and waits for all R. Then it decides its own pair
-// of the round from the two published energies, the same decision the pair's other replica
-// and the exchange kernel take, and moves to its new slot. The pair's lower replica keeps
-// the pair counters and the log; each replica writes its own labels; replica 0 of the
-// ensemble advances xround. No replica reads the label arrays inside the launch, and a
-// buffer is rewritten two rounds later, after every replica has passed the round between.
-// slot (local) is updated; false if the wait gave up.
+// ensemble e calls it, lane 0 does the work). A round only couples the two replicas of each
+// pair, so a replica waits for its partner alone. It writes its energy under its temperature
+// slot into the round's buffer (xr mod 4), then the slot's stamp xr + 1; waits until the
+// partner slot's stamp reaches xr + 1; reads the partner's energy and takes the pair's
+// decision, the same one the partner and the exchange kernel take. The lower replica of a
+// pair keeps its counters and log entry; each replica writes its own labels; an unpaired
+// replica (an end slot of the round) neither publishes nor waits.
+// Buffer reuse: a buffer is rewritten four rounds later. The replica holding slot s cannot
+// finish round x + 2 until the holder of the slot that was s's partner in round x publishes
+// round x + 2 (or has taken part in a swap in round x + 1), which that replica does only
+// after it has read round x; so the round-x value is read before the round x + 4 write.
+// Returns false if the wait gave up; slot (local) is updated, xr advanced.
 __device__ __forceinline__ bool ensemble_exchange(const State& S, const EnsDev& ed, int e, int g, int r, double E,
                                                   int64_t sw, int64_t& xr, int& slot, int lane) {
     const int base = ed.rep_base, R = ed.R;
-    double* buf = S.xE + (size_t)(xr & 1) * S.n_reps + base;
-    if (lane == 0) {
-        __stcg(buf + slot, E);
-        __threadfence();
-        atomicAdd(&S.xarrive[e], 1ull);
-    }
-    const bool ok = wait_at_least(&S.xarrive[e], (unsigned long long)R * (unsigned long long)(xr + 1), lane);
-    if (!ok) return false;
-    int ns = slot;
+    int ns = slot, ok = 1;
     if (lane == 0) {
         const int q = (int)(xr & 1);
         const bool lower = ((slot - q) & 1) == 0 && slot >= q && slot + 1 < R;
@@ -185,30 +165,45 @@ __device__ __forceinline__ bool ensemble_exchange(const State& S, const EnsDev& 
                          ? S.log_x + (size_t)(s_log - S.log_s0) * S.n_reps + base
                          : nullptr;
         if (lower || upper) {
-            const int t = lower ? slot : slot - 1;
-            const double arg = (__ldcg(buf + t) - __ldcg(buf + t + 1)) * (S.beta[base + t] - S.beta[base + t + 1]);
-            const u4 w = philox(u4{(uint32_t)t, (uint32_t)xr, 0u, ed.ens_id | (kTagExch << 24)}, (uint32_t)ed.seed,
-                                (uint32_t)(ed.seed >> 32));
-            const bool acc = exchange_accept(arg, w.x >> 8);
-            if (acc) ns = lower ? t + 1 : t;
-            if (lower) {
-                S.ex_att[base + t] += 1ull;
-                if (acc) S.ex_acc[base + t] += 1ull;
+            double* buf = S.xE + (size_t)(xr & 3) * S.n_reps + base;
+            const int t = lower ? slot : slot - 1, other = lower ? slot + 1 : slot - 1;
+            __stcg(buf + slot, E);
+            __threadfence();
+            atomicExch(&S.xstamp[base + slot], (unsigned long long)(xr + 1));
+            const unsigned long long need = (unsigned long long)(xr + 1) + (unsigned long long)__ldcg(&S.xhold[e]);
+            long long it = 0;
+            while (*(volatile unsigned long long*)&S.xstamp[base + other] < need) {
+                if (++it > kWaitPolls) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
             }
-            if (xo) xo[slot] = lower ? (acc ? 1 : 0) : -1;
+            if (ok) {
+                __threadfence();
+                const double eo = __ldcg(buf + other);
+                const double arg = ((lower ? E : eo) - (lower ? eo : E)) * (S.beta[base + t] - S.beta[base + t + 1]);
+                const u4 w = philox(u4{(uint32_t)t, (uint32_t)xr, 0u, ed.ens_id | (kTagExch << 24)},
+                                    (uint32_t)ed.seed, (uint32_t)(ed.seed >> 32));
+                const bool acc = exchange_accept(arg, w.x >> 8);
+                if (acc) ns = lower ? t + 1 : t;
+                if (lower) {
+                    S.ex_att[base + t] += 1ull;
+                    if (acc) S.ex_acc[base + t] += 1ull;
+                }
+                if (xo) xo[slot] = lower ? (acc ? 1 : 0) : -1;
+            }
         } else if (xo) {
             xo[slot] = -1;
         }
-        S.rep_of_temp[base + ns] = r;
-        S.temp_of_rep[g] = ns;
-        if (r == 0) {
-            S.ens[e].xround = xr + 1;
-            S.ens[e].last_x_sweep = sw;
+        if (ok) {
+            S.rep_of_temp[base + ns] = r;
+            S.temp_of_rep[g] = ns;
         }
     }
     slot = __shfl_sync(0xffffffffu, ns, 0);
     ++xr;
-    return true;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 // End of one sweep of replica g (all lanes of its warp call it): the periodic FP64

@@ -43,7 +43,13 @@ __global__ void __maxnreg__(U >= 32 ? 248 : 168) k_sweep_reg(State S, int chunk)
     const int N = rd.N;
     int64_t s = S.rep_sweep[g];
     int64_t s_end = min(ed.target, s + (int64_t)chunk);
-    if (s >= s_end) return;
+    if (s >= s_end) {
+        if (S.xin && lane == 0) {
+            S.xrep[g] = ed.xround;
+            S.xrep[S.n_reps + g] = ed.last_x_sweep;
+        }
+        return;
+    }
 
     float4* P = smem;                                  // [nmax] the chain
     float4* D0 = P + S.nmax;                           // [32] move: bead | bond flags << 16, displacement
@@ -71,7 +77,7 @@ __global__ void __maxnreg__(U >= 32 ? 248 : 168) k_sweep_reg(State S, int chunk)
     int slot = S.temp_of_rep[g];
     int gs = rd.slot_base + slot;
     float Tf = S.Tf[gs];
-    int64_t xr = S.xin ? S.ens[rd.ens].xround : 0;  // exchange rounds of the ensemble (in-kernel exchange)
+    int64_t xr = ed.xround, lxs = ed.last_x_sweep;  // rounds done, sweep of the last (in-kernel exchange)
     const uint32_t k0 = (uint32_t)ed.seed, k1 = (uint32_t)(ed.seed >> 32);
     const uint32_t c3 = ed.ens_id | (kTagMove << 24);
     const bool ljb = ed.lj_bonded != 0;
@@ -276,6 +282,7 @@ __global__ void __maxnreg__(U >= 32 ? 248 : 168) k_sweep_reg(State S, int chunk)
             }
             gs = rd.slot_base + slot;
             Tf = S.Tf[gs];
+            lxs = s + 1;
         }
     }
     __syncwarp();
@@ -283,6 +290,10 @@ __global__ void __maxnreg__(U >= 32 ? 248 : 168) k_sweep_reg(State S, int chunk)
     if (lane == 0) {
         S.E[g] = E;
         S.rep_sweep[g] = s_end;
+        if (S.xin) {
+            S.xrep[g] = xr;
+            S.xrep[S.n_reps + g] = lxs;
+        }
     }
 }
 

@@ -1,7 +1,7 @@
 """Build the CUDA library in-tree: paper_1107_3490_gb300/_lib/libptgb.so (sm_103a only).
 
 Each translation unit is compiled in parallel with nvcc, then linked with the static CUDA
-runtime, so the library needs nothing but the driver at run time.
+runtime, so the library needs nothing but the CUDA driver at run time.
 """
 from __future__ import annotations
 

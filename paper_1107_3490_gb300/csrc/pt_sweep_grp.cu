@@ -9,16 +9,19 @@
 // chain in registers): its row, its bonds, and the bracket of its dE from the exact
 // fixed-point sums of the lane bounds. Lane l < i of warp i forms the correction of move i
 // for an acceptance of move l: the term of move i's bead against bead k_l at its proposed
-// position minus the term against its old position (LJ, or FENE plus bonded LJ when the
-// beads are bonded), with its rounding bound. After one barrier warp 0 takes the decisions
-// in move order, one lane per move, adding for each accepted earlier move its correction
-// interval. A move whose threshold lies inside its interval ends the group; so does a move
-// whose value would rest on an inexact correction (a steep or bonded partner that moved):
-// it is evaluated again, against the updated chain, as the first move of the next group,
-// where an undecided move is decided on its value like kernel 4's. Then each accepted move
-// takes its FP32 dE value (the double-float remainder of its steep row pairs and bonds far
-// from r0 is added at the end of the sweep, as in kernel 4), every warp applies the accepted
-// moves to its registers, and the chain in shared memory is updated. The chain is therefore exactly that of pt_sweep_reg.cu, move for move.
+// position minus the term against its old position (LJ, computed beside the row, or FENE
+// plus bonded LJ when the beads are bonded), with its rounding bound. After one barrier every
+// warp takes the same decisions: first each move against its interval widened over every
+// subset of earlier acceptances (one pass and three ballots when all decide), else in move
+// order, one lane per move, adding for each accepted earlier move its correction interval.
+// A move whose threshold lies inside its interval ends the group; so does a move whose value
+// would rest on an inexact correction (a steep or bonded partner that moved): it is evaluated
+// again, against the updated chain, as the first move of the next group, where an undecided
+// move is decided on its value like kernel 4's. Then each accepted move takes its FP32 dE
+// value (the double-float remainder of its steep row pairs and bonds far from r0 is added at
+// the end of the sweep, as in kernel 4), every warp applies the accepted moves to its
+// registers, and the chain in shared memory is updated. The chain is therefore exactly that
+// of pt_sweep_reg.cu, move for move (up to decisions within the parity tolerance).
 #include "pt_sweep_f32.cuh"
 
 namespace ptgb {

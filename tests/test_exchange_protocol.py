@@ -106,3 +106,36 @@ def test_buffer_depth_three_also_suffices_and_two_does_not():
     with pytest.raises(AssertionError, match="buffer holds round"):
         for seed in range(200):
             _asynchronous(64, 40, energy, K=2, seed=seed)
+
+
+def test_exchange_decision_band_agrees_with_fp64():
+    """The exchange decision's FP32 fast path (accept iff u < exp(arg), arg < 0): expf of the
+    rounded argument, taken with an error of up to 2 ulp, decides only when u lies outside
+    the band ef (1 -+ m), m = (|af| + 8) 2^-23, with the band's ends rounded outward; inside it
+    FP64 exp decides. Over random and near-threshold draws the result equals the FP64 decision
+    u < exp(arg), and the fallback is rare for random draws."""
+    import numpy as np
+    rng = np.random.default_rng(5)
+    n = 400000
+    arg = -rng.uniform(0.0, 20.0, n) * rng.choice([1.0, 1e-3, 1e-7], n)
+    af = arg.astype(np.float32)
+    ef = np.exp(af.astype(np.float64)).astype(np.float32)  # correctly rounded float exp
+    ulp = np.spacing(ef)
+    ef = (ef + rng.integers(-2, 3, n).astype(np.float32) * ulp).astype(np.float32)  # 2-ulp error
+    m = ((np.abs(af) + np.float32(8.0)) * np.float32(2.0 ** -23)).astype(np.float32)
+    m = np.nextafter(m, np.float32(np.inf))
+    lo = np.nextafter((ef * (np.float32(1.0) - m)).astype(np.float32), np.float32(0.0))
+    hi = np.nextafter((ef * (np.float32(1.0) + m)).astype(np.float32), np.float32(np.inf))
+    # u on the 24-bit grid: half at random, half within a few grid steps of exp(arg)
+    w = rng.integers(0, 1 << 24, n)
+    near = rng.random(n) < 0.5
+    w[near] = np.clip(np.floor(np.exp(arg[near]) * 2.0 ** 24).astype(np.int64) + rng.integers(-3, 4, near.sum()),
+                      0, (1 << 24) - 1)
+    u = w.astype(np.float64) * 2.0 ** -24
+    uf = u.astype(np.float32)
+    assert np.array_equal(uf.astype(np.float64), u)  # exact
+    fast = np.where(uf < lo, 1, np.where(uf > hi, 0, -1))
+    exact = (u < np.exp(arg)).astype(int)
+    decided = fast >= 0
+    assert np.array_equal(fast[decided], exact[decided])
+    assert decided[~near].mean() > 0.999  # the FP64 fallback is rare for random draws

@@ -36,7 +36,7 @@ UNIT = "updates/s"
 # DRAM bytes read + written per sweep on this workload (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch of the kernel as it stands, divided by the sweeps that
 # launch ran), keyed by (kernel, launch mode); pairs without a current capture report null
-TRAFFIC_BYTES = {("k_sweep_grp", 1): 2220}
+TRAFFIC_BYTES = {("k_sweep_grp", 1): 2220, ("k_sweep_reg", 1): 2192}
 WORKLOAD = (f"PT polymer N={N_BEADS} beads, {N_REP} replicas at T geometric {T_MIN}-{T_MAX}, "
             f"{N_ENS} ensembles (seeds 1-{N_ENS}) per GPU, delta 0.3, exchange every sweep, "
             f"FP64 recompute every 1000 sweeps, 4096 FP64 bins/slot; 1 step = {SWEEPS_PER_STEP} sweeps")

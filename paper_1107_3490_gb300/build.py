@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libptgb.so")
-SOURCES = ["pt_kernels.cu", "pt_sweep_reg.cu", "pt_sweep_grp.cu", "pt_api.cu", "pt_noalloc.cu", "pt_server.cu", "pt_wham.cpp", "pt_peak.cu"]
+SOURCES = ["pt_kernels.cu", "pt_sweep_reg.cu", "pt_sweep_grp.cu", "pt_sweep_cta.cu", "pt_api.cu", "pt_noalloc.cu", "pt_server.cu", "pt_wham.cpp", "pt_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

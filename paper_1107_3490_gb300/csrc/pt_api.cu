@@ -292,6 +292,10 @@ void drop_graph(pt_ctx* h) {
 // N = 30: 34.6 / 27.9 / 27.9; N = 60: 68.2 / 46.0 / 43.0; N = 1000: kernel 2 945, kernel 5
 // 658. The chain in registers of one warp wins for short chains, a CTA of warps each taking
 // one move of a group from about 40 beads to the register limit, the team kernel beyond.
+// Kernels with a persistent (cooperative) mode, and the longest chain each one holds.
+bool has_persistent(int v) { return v == kSweepReg || v == kSweepGrp || v == kSweepCta; }
+int variant_max_n(int v) { return v == kSweepCta ? kCtaMaxN : (v == kSweepReg || v == kSweepGrp) ? kRegMaxN : 1 << 30; }
+
 int default_variant(int nmax) {
     return nmax <= 40 ? kSweepReg : nmax <= kRegMaxN ? kSweepGrp : kSweepTeam;
 }
@@ -695,10 +699,10 @@ extern "C" int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every) {
 extern "C" int pt_set_sweep_kernel(pt_ctx* h, int variant) {
     int rc = check_usable(h);
     if (rc) return rc;
-    if (variant < kSweepSimple || variant > kSweepGrp)
+    if (variant < kSweepSimple || variant > kSweepCta)
         return fail(PT_EINVAL, "unknown sweep kernel %d", variant);
-    if ((variant == kSweepReg || variant == kSweepGrp) && h->nmax > kRegMaxN)
-        return fail(PT_EINVAL, "sweep kernel %d holds chains of at most %d beads", variant, kRegMaxN);
+    if (h->nmax > variant_max_n(variant))
+        return fail(PT_EINVAL, "sweep kernel %d holds chains of at most %d beads", variant, variant_max_n(variant));
     if ((rc = sync_and_check(h))) return rc;
     const int warps = sweep_warps_per_block(h->nmax, h->G, h->num_sms, variant);
     const size_t smem = sweep_smem_bytes(h->nmax, warps, variant);
@@ -734,7 +738,7 @@ extern "C" int pt_set_launch_mode(pt_ctx* h, int mode) {
 
 extern "C" int pt_get_launch_mode(const pt_ctx* h) {
     if (!h) return -1;
-    return (h->launch_mode == 1 && h->coop_ok && (h->variant == kSweepReg || h->variant == kSweepGrp)) ? 1 : 0;
+    return (h->launch_mode == 1 && h->coop_ok && has_persistent(h->variant)) ? 1 : 0;
 }
 
 namespace {
@@ -793,15 +797,15 @@ extern "C" int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen) 
     CK(h, cudaEventCreate(&b));
     int best = h->variant, best_mode = h->launch_mode;
     float best_ms = 1e30f;
-    const int variants[] = {kSweepSimple, kSweepLookahead, kSweepTeam, kSweepWpm, kSweepReg, kSweepGrp};
+    const int variants[] = {kSweepSimple, kSweepLookahead, kSweepTeam, kSweepWpm, kSweepReg, kSweepGrp, kSweepCta};
     for (int v : variants) {
-        if ((v == kSweepReg || v == kSweepGrp) && h->nmax > kRegMaxN) continue;
+        if (h->nmax > variant_max_n(v)) continue;
         if (sweep_smem_bytes(h->nmax, sweep_warps_per_block(h->nmax, h->G, h->num_sms, v), v) > (size_t)h->smem_optin)
             continue;
         if ((rc = pt_set_sweep_kernel(h, v))) break;
-        // kernels 4 and 5 also in both launch modes (persistent where the grid fits)
+        // kernels 4, 5 and 6 also in both launch modes (persistent where the grid fits)
         for (int mode = 1; mode >= 0; --mode) {
-            if (mode == 1 && !(h->coop_ok && (v == kSweepReg || v == kSweepGrp))) continue;
+            if (mode == 1 && !(h->coop_ok && has_persistent(v))) continue;
             h->launch_mode = mode;
             if ((rc = pt_sweep(h, 2, 1))) break;  // warm-up (and graph capture)
             CK(h, cudaEventRecord(a, h->stream));

@@ -81,8 +81,12 @@ struct State {
 // takes the double-float work only where a decision or an accepted energy needs it.
 // kSweepGrp gives each replica a CTA of 4-8 warps holding the chain in registers, each warp
 // evaluating one move of a group of consecutive moves on distinct beads (N <= kRegMaxN).
-enum : int { kSweepSimple = 0, kSweepLookahead = 1, kSweepTeam = 2, kSweepWpm = 3, kSweepReg = 4, kSweepGrp = 5 };
+// kSweepCta gives each replica a CTA whose threads each hold a slice of the chain and
+// evaluate every move of a group against it, in packed FP32x2 (N <= kCtaMaxN).
+enum : int { kSweepSimple = 0, kSweepLookahead = 1, kSweepTeam = 2, kSweepWpm = 3, kSweepReg = 4, kSweepGrp = 5,
+             kSweepCta = 6 };
 constexpr int kRegMaxN = 1024;
+constexpr int kCtaMaxN = 4096;
 int reg_slots(int nmax);
 size_t reg_smem_bytes(int nmax);
 cudaError_t launch_sweep_reg(const State& s, int chunk, cudaStream_t st);
@@ -94,6 +98,13 @@ cudaError_t configure_sweep_grp(int nmax);
 cudaError_t launch_sweep_grp(const State& s, int chunk, cudaStream_t st);
 bool grp_coop_fits(const State& s, int nmax, int num_sms);
 cudaError_t launch_sweep_grp_coop(const State& s, int chunk, cudaStream_t st);
+void cta_shape(int nmax, int& u, int& w);
+int cta_warps(int nmax);
+size_t cta_smem_bytes(int nmax);
+cudaError_t configure_sweep_cta(int nmax);
+cudaError_t launch_sweep_cta(const State& s, int chunk, cudaStream_t st);
+bool cta_coop_fits(const State& s, int nmax, int num_sms);
+cudaError_t launch_sweep_cta_coop(const State& s, int chunk, cudaStream_t st);
 int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant);
 size_t sweep_smem_bytes(int nmax, int warps, int variant);
 cudaError_t configure_sweep(int nmax, int warps, int variant);  // per context, before any capture

@@ -917,6 +917,7 @@ __global__ void k_energy_final(const double* __restrict__ scratch, int n_conf, i
 
 // ---- launchers ----------------------------------------------------------------------------
 size_t sweep_smem_bytes(int nmax, int warps, int variant) {
+    if (variant == kSweepCta) return cta_smem_bytes(nmax);
     if (variant == kSweepReg) return reg_smem_bytes(nmax);
     if (variant == kSweepGrp) return grp_smem_bytes(nmax, warps);
     if (variant == kSweepTeam) return team_smem_bytes(nmax, warps);
@@ -931,6 +932,7 @@ int team_warps(int nmax) { return nmax <= 48 ? 1 : nmax <= 160 ? 2 : nmax <= 480
 int wpm_warps(int nmax) { return nmax <= 24 ? 2 : nmax <= 400 ? 4 : 8; }
 
 int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant) {
+    if (variant == kSweepCta) return cta_warps(nmax);
     if (variant == kSweepReg) return 1;
     if (variant == kSweepGrp) return grp_warps(nmax);
     if (variant == kSweepTeam) return team_warps(nmax);
@@ -944,6 +946,7 @@ int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant) {
 
 cudaError_t configure_sweep(int nmax, int warps, int variant) {
     const size_t smem = sweep_smem_bytes(nmax, warps, variant);
+    if (variant == kSweepCta) return configure_sweep_cta(nmax);
     if (variant == kSweepReg) return nmax <= kRegMaxN ? cudaSuccess : cudaErrorInvalidValue;
     if (variant == kSweepGrp) return nmax <= kRegMaxN ? configure_sweep_grp(nmax) : cudaErrorInvalidValue;
     if (smem <= 48 * 1024) return cudaSuccess;
@@ -970,6 +973,7 @@ cudaError_t configure_sweep(int nmax, int warps, int variant) {
 }
 
 cudaError_t launch_sweep(const State& s, int chunk, int warps, int variant, cudaStream_t st) {
+    if (variant == kSweepCta) return launch_sweep_cta(s, chunk, st);
     if (variant == kSweepReg) return launch_sweep_reg(s, chunk, st);
     if (variant == kSweepGrp) return launch_sweep_grp(s, chunk, st);
     const size_t smem = sweep_smem_bytes(s.nmax, warps, variant);
@@ -999,6 +1003,7 @@ cudaError_t launch_sweep(const State& s, int chunk, int warps, int variant, cuda
 }
 
 bool sweep_coop_fits(const State& s, int nmax, int variant, int num_sms) {
+    if (variant == kSweepCta) return cta_coop_fits(s, nmax, num_sms);
     if (nmax > kRegMaxN) return false;
     if (variant == kSweepReg) return reg_coop_fits(s, nmax, num_sms);
     if (variant == kSweepGrp) return grp_coop_fits(s, nmax, num_sms);
@@ -1006,6 +1011,7 @@ bool sweep_coop_fits(const State& s, int nmax, int variant, int num_sms) {
 }
 
 cudaError_t launch_sweep_coop(const State& s, int chunk, int variant, cudaStream_t st) {
+    if (variant == kSweepCta) return launch_sweep_cta_coop(s, chunk, st);
     if (variant == kSweepReg) return launch_sweep_reg_coop(s, chunk, st);
     if (variant == kSweepGrp) return launch_sweep_grp_coop(s, chunk, st);
     return cudaErrorInvalidValue;

@@ -96,6 +96,49 @@ __device__ __forceinline__ unsigned bond_flags(const BondF& b) {
     return (b.inexact ? 1u : 0u) | (b.edge ? 2u : 0u) | (b.low_only ? 4u : 0u);
 }
 
+// LJ term (Eqs. 1-2) of the move p -> pn against partner q in FP32 with its error bound:
+// the arithmetic of row_pass for one slot.
+struct PairF {
+    float t, e;
+    bool steep;
+};
+__device__ __forceinline__ PairF lj_pair_f32(float4 q, float3 p, float3 pn) {
+    const float dxo = __fsub_rn(q.x, p.x), dyo = __fsub_rn(q.y, p.y), dzo = __fsub_rn(q.z, p.z);
+    const float dxn = __fsub_rn(q.x, pn.x), dyn = __fsub_rn(q.y, pn.y), dzn = __fsub_rn(q.z, pn.z);
+    const float r2o = __fmaf_rn(dzo, dzo, __fmaf_rn(dyo, dyo, __fmul_rn(dxo, dxo)));
+    const float r2n = __fmaf_rn(dzn, dzn, __fmaf_rn(dyn, dyn, __fmul_rn(dxn, dxn)));
+    const float io = rcp_approx(fminf(r2o, kRc2f)), in = rcp_approx(fminf(r2n, kRc2f));
+    const float xo = __fmul_rn(__fmul_rn(io, io), io), xn = __fmul_rn(__fmul_rn(in, in), in);
+    PairF r;
+    r.t = __fmul_rn(__fsub_rn(xn, xo), __fmaf_rn(kAf, __fadd_rn(xn, xo), -kBf));
+    const float w = __fadd_rn(fabsf(__fmul_rn(__fmaf_rn(2.f * kAf, xo, -kBf), xo)),
+                              fabsf(__fmul_rn(__fmaf_rn(2.f * kAf, xn, -kBf), xn)));
+    r.e = __fmaf_rn(kDeltaX, w, 4.f * kEps0 * fabsf(r.t));
+    r.steep = fminf(r2o, r2n) < kSteepTeam2f;
+    return r;
+}
+
+// Correction of a move (p -> pn) for an accepted move of a group partner from qo to qn:
+// term(qn) - term(qo), LJ or (bonded) FENE plus bonded LJ. Flags: bit 0 inexact (the
+// accurate value needs double-float), bit 1 undecidable (a bond at the FENE wall).
+__device__ __forceinline__ void correction_f32(float4 qo, float4 qn, float3 p, float3 pn, bool bonded, bool ljb,
+                                               float& d, float& e, unsigned& fl) {
+    if (bonded) {
+        // the difference of two FENE terms can cancel far below their size: its value is
+        // always taken in double-float (the bound still serves the decision)
+        const BondF a = bond_f32(qn, p, pn, ljb), b = bond_f32(qo, p, pn, ljb);
+        fl = 1u | ((a.edge || b.edge || a.low_only || b.low_only) ? 2u : 0u);
+        d = __fsub_rn(a.t, b.t);  // +inf when the new bond breaks
+        e = __fadd_ru(__fadd_ru(a.e, b.e), 2.f * kEps0 * fabsf(d) < __int_as_float(0x7f800000) ? 2.f * kEps0 * fabsf(d) : 0.f);
+    } else {
+        const PairF a = lj_pair_f32(qn, p, pn), b = lj_pair_f32(qo, p, pn);
+        fl = (a.steep || b.steep) ? 1u : 0u;
+        d = __fsub_rn(a.t, b.t);
+        e = __fadd_ru(__fadd_ru(a.e, b.e), 2.f * kEps0 * fabsf(d));
+    }
+}
+
+
 }  // namespace
 
 // Row of the moved bead k over this lane's partners: sums of the ordinary and of the steep

@@ -210,7 +210,7 @@ def test_autotune_leaves_the_state_untouched():
         before = _state(h)
         c0 = pt.pt_counters(h)
         v = pt.pt_autotune(h, 4, force=True)
-        assert v in (0, 1, 2, 3, 4, 5) and pt.pt_get_sweep_kernel(h) == v
+        assert v in (0, 1, 2, 3, 4, 5, 6) and pt.pt_get_sweep_kernel(h) == v
         _same(_state(h), before)
         assert pt.pt_counters(h) == c0
         assert pt.pt_autotune(h, 4) == v  # cached
@@ -220,7 +220,7 @@ def test_autotune_leaves_the_state_untouched():
         pt.pt_destroy(h)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_every_kernel_keeps_the_batch_bit_identical_to_separate_runs(variant):
     """Per-ensemble results do not depend on which ensembles share the launch."""
     specs = [(20, 4, 1, 0), (45, 7, 2, 1)]
@@ -246,7 +246,7 @@ def test_every_kernel_keeps_the_batch_bit_identical_to_separate_runs(variant):
         po += 3 * R * N
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_the_move_log_does_not_change_the_chain(variant):
     """With the per-move log on, kernels may evaluate more terms accurately (kernel 4 refines
     every move with a steep pair); the chain itself must be the same bit for bit."""
@@ -268,9 +268,9 @@ def test_the_move_log_does_not_change_the_chain(variant):
     a, b = out
     assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["rot"], b["rot"])
     assert np.array_equal(a["hist"], b["hist"])
-    if variant in (4, 5):
+    if variant in (4, 5, 6):
         # with the log on, accepted dE values are refined at once instead of at the end of
-        # the sweep (and kernel 5 ends groups differently): equal within the rounding
+        # the sweep (and kernels 5 and 6 end groups differently): equal within the rounding
         np.testing.assert_allclose(a["E"], b["E"], rtol=0, atol=1e-5)
     else:
         assert np.array_equal(a["E"], b["E"])
@@ -278,7 +278,7 @@ def test_the_move_log_does_not_change_the_chain(variant):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("variant", [4, 5])
+@pytest.mark.parametrize("variant", [4, 5, 6])
 @pytest.mark.parametrize("xe", [1, 3])
 def test_persistent_launch_runs_the_same_chain(variant, xe):
     """One cooperative launch with the exchange rounds inside the kernel against per-sweep
@@ -324,7 +324,8 @@ def test_persistent_launch_continues_from_a_checkpoint():
         pt.pt_destroy(h)
 
 
-@pytest.mark.parametrize("variant,mode,xe", [(4, 1, 1), (5, 1, 3), (5, 0, 1), (2, 0, 1), (2, 0, 4)])
+@pytest.mark.parametrize("variant,mode,xe", [(4, 1, 1), (5, 1, 3), (5, 0, 1), (6, 1, 1), (6, 0, 3), (2, 0, 1),
+                                             (2, 0, 4)])
 def test_kernel_timing_in_every_launch_path(variant, mode, xe):
     """Kernel timing brackets persistent launches, graph replays and direct launches alike,
     and does not change the chain."""
@@ -358,7 +359,7 @@ def test_fp32_fma_rate_is_near_the_derived_peak():
         pt.pt_fp32_fma_rate(0, 0)
 
 
-@pytest.mark.parametrize("variant", [4, 5])
+@pytest.mark.parametrize("variant", [4, 5, 6])
 def test_exchange_barrier_wait_gives_up_and_the_context_recovers(variant):
     """A stalled in-kernel exchange barrier (one arrival short, made on the host): every
     replica's bounded wait gives up, the call reports PT_ETIMEOUT once, and after a restore the

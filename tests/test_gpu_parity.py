@@ -15,7 +15,8 @@ from tests import parity
 pytestmark = pytest.mark.gpu
 
 KERNELS = {0: "one move at a time", 1: "lookahead groups", 2: "team of warps per replica",
-           3: "warp per move of a group", 4: "registers, deferred double-float", 5: "groups of moves, registers"}
+           3: "warp per move of a group", 4: "registers, deferred double-float", 5: "groups of moves, registers",
+           6: "groups of moves, CTA-wide packed rows"}
 
 
 @pytest.fixture(params=sorted(KERNELS), ids=lambda v: f"kernel{v}")
@@ -198,7 +199,7 @@ def test_kernels_agree_on_a_hot_dense_case():
         assert np.all(d <= 2e-6 + 2e-5 * np.abs(a["de"][fin]))
 
 
-@pytest.mark.parametrize("variant", [4, 5])
+@pytest.mark.parametrize("variant", [4, 5, 6])
 def test_benchmark_configuration_sampled(variant):
     """The benchmark's workload in its launch configuration: four ensembles (seeds 1-4) of
     N = 100 x 64 replicas, T 0.2-3.0, 4096 bins, in one batched context; ensembles 0 and 3
@@ -246,16 +247,17 @@ def pt_default_kernel(N):
         pt.pt_destroy(h)
 
 
-@pytest.mark.parametrize("variant", [0, 2, 3])
+@pytest.mark.parametrize("variant", [0, 2, 3, 6])
 @pytest.mark.parametrize("N", [2048, 8192])
 def test_longest_chains(N, variant):
     """Chains beyond the register kernels' 1024 beads, up to the largest N the library takes
-    (the warp-per-move kernel's shared memory does not fit 8192 beads: a clean PT_EINVAL)."""
-    if variant == 3 and N == 8192:
+    (the warp-per-move kernel's shared memory does not fit 8192 beads, and kernel 6 holds at
+    most 4096: a clean PT_EINVAL)."""
+    if variant in (3, 6) and N == 8192:
         h = pt.pt_create(N, 2, np.array([1.0, 2.0]), 1)
         try:
             with pytest.raises(pt.PtError):
-                pt.pt_set_sweep_kernel(h, 3)
+                pt.pt_set_sweep_kernel(h, variant)
             pt.pt_sweep(h, 1, 1)  # still usable with its own kernel
         finally:
             pt.pt_destroy(h)
@@ -275,3 +277,17 @@ def test_register_kernels_reject_longer_chains():
         assert pt.pt_counters(h, 0)[0] == 0
     finally:
         pt.pt_destroy(h)
+
+
+@pytest.mark.parametrize("N", [300, 1000])
+def test_long_chains_at_128_replicas_ten_sweeps(N):
+    """The long-chain configurations (N = 300 and 1000, 128 replicas, T 0.2-3.0, exchange every
+    sweep) with the CTA-wide group kernel that the benchmark times: ten sweeps move for move
+    against the oracle, in the persistent launch the benchmark uses."""
+    rep, out, orc = _run(N, 128, 10, seed=1, tmin=0.2, variant=6)
+    assert rep.ok, rep.failures
+    assert rep.moves_compared > 128 * N
+    print(f"N={N}: {rep.sweeps_compared} sweeps, {rep.moves_compared} moves, max dE err/tol "
+          f"{rep.max_ratio:.3f}, divergence {rep.divergence}")
+    if rep.divergence is None:
+        _full_match(rep, out, orc, 10)

@@ -449,6 +449,11 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
                 if (__syncthreads_or(tid == 0 && CNT[0] > kPendCta / 2)) flush();
                 // ---- control warp: totals in warp order, brackets, decisions, accepted values and
                 // the chain in shared memory
+                unsigned am = 0u;    // control warp: accepted moves, decided moves, value of move
+                int nd0 = 0;         // lane, and the bond partners of an accepted move lane
+                float vi = 0.f;
+                bool acc_i = false;
+                float4 qm = make_float4(0.f, 0.f, 0.f, 0.f), qp = qm;
                 if (ctl) {
                     float tot = 0.f;
 #pragma unroll
@@ -470,28 +475,18 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
                     }
                     __syncwarp();
                     if (lane < kG) NEARM[lane] = 0u;
-                    unsigned am;
-                    int nd0;
-                    float vi;
                     group_decide(w, lane, logging, lo0, hi0, part, th, nm, CX + lane * kCxStride, am, nd0, vi);
-                    if (!logging && nd0 > 0) {
-                        for (unsigned m = am; m; m &= m - 1) {
-                            dsum = df_add(dsum, df{__shfl_sync(kFull, vi, __ffs(m) - 1), 0.f});
-                            ++nacc;
-                        }
-                        if (lane < nd0 && ((am >> lane) & 1u)) {
-                            const int k = rec_k(lane);
-                            const float3 p = rec_p(lane), pn = rec_pn(lane);
-                            // inexact bonds of an accepted move with an FP32 value: deferred terms
-                            // (no bond partner of an accepted move moved in the group: that
-                            // correction is inexact and would have ended the group)
-                            if (bf & 7u) {
-                                const float kind = ljb ? kPendBondLJ : kPendBond;
-                                if (k > 0) defer(make_float4(P[k - 1].x, P[k - 1].y, P[k - 1].z, kind), p, pn);
-                                if (k + 1 < N) defer(make_float4(P[k + 1].x, P[k + 1].y, P[k + 1].z, kind), p, pn);
-                            }
-                            P[k] = make_float4(pn.x, pn.y, pn.z, 0.f);
-                        }
+                    // the accepted moves into the chain in shared memory, before the barrier that
+                    // hands it to the row threads; their values and deferred bond terms after it
+                    acc_i = !logging && lane < nd0 && ((am >> lane) & 1u);
+                    if (acc_i) {
+                        const int k = rec_k(lane);
+                        const float3 pn = rec_pn(lane);
+                        // no bond partner of an accepted move moved in the group: that
+                        // correction is inexact and would have ended the group
+                        if (k > 0) qm = P[k - 1];
+                        if (k + 1 < N) qp = P[k + 1];
+                        P[k] = make_float4(pn.x, pn.y, pn.z, 0.f);
                     }
                     if (lane == 0) {
                         CNT[2] = (int)am;
@@ -499,6 +494,22 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
                     }
                 }
                 __syncthreads();  // the second group barrier: decisions and the chain are out
+                if (ctl) {
+                    if (!logging && nd0 > 0) {
+                        for (unsigned m = am; m; m &= m - 1) {
+                            dsum = df_add(dsum, df{__shfl_sync(kFull, vi, __ffs(m) - 1), 0.f});
+                            ++nacc;
+                        }
+                        // inexact bonds of an accepted move with an FP32 value: deferred terms
+                        if (acc_i && (bf & 7u)) {
+                            const int k = rec_k(lane);
+                            const float3 p = rec_p(lane), pn = rec_pn(lane);
+                            const float kind = ljb ? kPendBondLJ : kPendBond;
+                            if (k > 0) defer(make_float4(qm.x, qm.y, qm.z, kind), p, pn);
+                            if (k + 1 < N) defer(make_float4(qp.x, qp.y, qp.z, kind), p, pn);
+                        }
+                    }
+                }
                 unsigned amask = (unsigned)CNT[2];
                 int nd = CNT[3];
                 const bool need0 = nd == 0 || logging;

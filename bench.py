@@ -1,12 +1,13 @@
 """Benchmark: single-bead Metropolis updates per second of the parallel-tempering engine.
 
-Workload (one GPU): 4 independent PT ensembles (seeds 1-4) of an N = 100 bead chain with
-64 replicas at geometric temperatures 0.2-3.0, displacement half-width 0.3, an exchange
-round after every sweep, an FP64 full-energy recompute every 1000 sweeps and 4096 FP64
-histogram bins per temperature slot. One step = 1000 sweeps of all four ensembles
-(4 x 64 x 100 x 1000 = 25.6 M single-bead updates); 100 steps are the whole 1e5-sweep run.
-Under torchrun every rank runs its own four ensembles (seeds 4 rank + 1 ... 4 rank + 4):
-weak scaling, no collective on the data path.
+Default workload (one GPU, the long-chain configuration): one PT ensemble of an N = 1000 bead
+chain with 128 replicas at geometric temperatures 0.2-3.0, displacement half-width 0.3, an
+exchange round after every sweep, an FP64 full-energy recompute every 1000 sweeps and 4096
+FP64 histogram bins per temperature slot. One step = 1000 sweeps (128 x 1000 x 1000 = 128 M
+single-bead updates); 20 steps are the whole 2e4-sweep run. ``--workload paper-scale`` runs
+the N = 100 configuration instead: 4 ensembles (seeds 1-4) of 64 replicas, one step = 1000
+sweeps of all four. Under torchrun every rank runs its own ensembles (seeds offset by the
+rank): weak scaling, no collective on the data path.
 
 Prints one JSON line (see the repository's benchmark contract). ``--impl reference`` times
 the FP64 CPU oracle instead, on bounded samples of the same workload.
@@ -26,24 +27,42 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-N_BEADS, N_REP, N_ENS, T_MIN, T_MAX = 100, 64, 4, 0.2, 3.0
+T_MIN, T_MAX = 0.2, 3.0
 SWEEPS_PER_STEP = 1000
-FLOPS_PER_PAIR = 15  # FP32 flops per pair evaluation (FMA = 2), see the design notes
+# FP32 flops per pair evaluation (FMA = 2): 3 subtractions for the coordinate differences, 5
+# for r^2 (a multiply and two FMAs), 1 for sigma^2 / r^2, 2 multiplies for the sixth power, 3
+# for s^6 (s^6 - 1) minus the shift, 1 to accumulate; the reciprocal is not counted.
+FLOPS_PER_PAIR = 15
 METRIC = "single-bead Metropolis updates/sec (all replicas)"
 KERNEL_NAMES = {0: "k_sweep", 1: "k_sweep_la", 2: "k_sweep_team", 3: "k_sweep_wpm", 4: "k_sweep_reg",
-                5: "k_sweep_grp"}
+                5: "k_sweep_grp", 6: "k_sweep_cta"}
+KERNEL_DESC = {0: "warp per replica", 1: "lookahead groups of 8 moves", 2: "team of warps per replica",
+               3: "warp per move of a group", 4: "warp per replica, chain in registers, deferred double-float",
+               5: "CTA per replica, one warp per move of a group, chain in registers",
+               6: "CTA per replica, every thread a chain slice and a group of 16 moves in packed FP32x2, control warp"}
 UNIT = "updates/s"
-# DRAM bytes read + written per sweep on this workload (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch of the kernel as it stands, divided by the sweeps that
-# launch ran), keyed by (kernel, launch mode); pairs without a current capture report null
-TRAFFIC_BYTES = {("k_sweep_grp", 1): 2220, ("k_sweep_reg", 1): 2192}
-WORKLOAD = (f"PT polymer N={N_BEADS} beads, {N_REP} replicas at T geometric {T_MIN}-{T_MAX}, "
-            f"{N_ENS} ensembles (seeds 1-{N_ENS}) per GPU, delta 0.3, exchange every sweep, "
-            f"FP64 recompute every 1000 sweeps, 4096 FP64 bins/slot; 1 step = {SWEEPS_PER_STEP} sweeps")
+# The plain (one-context) workloads: beads, replicas, ensembles per GPU.
+PLAIN = {
+    "long": dict(N=1000, R=128, E=1, label="long chains (configuration 3)"),
+    "paper-scale": dict(N=100, R=64, E=4, label="paper-scale (configuration 2)"),
+}
+# DRAM bytes read + written per sweep (ncu dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch of the kernel as it stands, divided by the sweeps that launch ran), keyed by
+# (workload, kernel, launch mode); pairs without a current capture report null
+TRAFFIC_BYTES = {}
 
 
-def updates_per_step(n_ens=N_ENS):
-    return n_ens * N_REP * N_BEADS * SWEEPS_PER_STEP
+def workload_text(w):
+    c = PLAIN[w]
+    ens = f"{c['E']} ensembles (seeds 1-{c['E']})" if c["E"] > 1 else "1 ensemble (seed 1)"
+    return (f"PT polymer N={c['N']} beads, {c['R']} replicas at T geometric {T_MIN}-{T_MAX}, {ens} per GPU, "
+            f"delta 0.3, exchange every sweep, FP64 recompute every 1000 sweeps, 4096 FP64 bins/slot; "
+            f"1 step = {SWEEPS_PER_STEP} sweeps")
+
+
+def updates_per_step(w):
+    c = PLAIN[w]
+    return c["E"] * c["R"] * c["N"] * SWEEPS_PER_STEP
 
 
 def dist_env():
@@ -71,14 +90,15 @@ def reduce_max(value: float, dist, device=None) -> float:
     return float(t.item())
 
 
-def ensemble_params(rank: int):
+def ensemble_params(rank: int, w: str):
     from paper_1107_3490_gb300 import inputs, pt
+    c = PLAIN[w]
     made = []
-    for e in range(N_ENS):
-        seed = N_ENS * rank + e + 1
-        T = inputs.temperature_ladder(T_MIN, T_MAX, N_REP)
-        x0 = inputs.random_coil(N_BEADS, N_REP, seed, seed - 1)
-        made.append(pt.make_params(N_BEADS, T, seed, ensemble_id=seed - 1, init_positions=x0,
+    for e in range(c["E"]):
+        seed = c["E"] * rank + e + 1
+        T = inputs.temperature_ladder(T_MIN, T_MAX, c["R"])
+        x0 = inputs.random_coil(c["N"], c["R"], seed, seed - 1)
+        made.append(pt.make_params(c["N"], T, seed, ensemble_id=seed - 1, init_positions=x0,
                                    delta=0.3, recompute_every=1000, n_bins=4096))
     return made
 
@@ -138,15 +158,21 @@ def fp32_peak_tflops(num_sms: int, mhz: float) -> float:
     return num_sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
-def cpu_baseline(target_s: float = 15.0, threads: int | None = None):
-    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload:
-    ensemble seed 1 (N = 100, 64 replicas), exchange every sweep."""
+def _oracle_sample(w: str, threads: int):
     import oracle
     from paper_1107_3490_gb300 import inputs
+    c = PLAIN[w]
+    T = inputs.temperature_ladder(T_MIN, T_MAX, c["R"])
+    return oracle.OracleEnsemble(inputs.random_coil(c["N"], c["R"], 1, 0), T, 1, delta=0.3,
+                                 recompute_every=1000, n_bins=4096, threads=threads)
+
+
+def cpu_baseline(w: str, target_s: float = 15.0, threads: int | None = None):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload:
+    its ensemble seed 1, exchange every sweep."""
+    c = PLAIN[w]
     threads = threads or os.cpu_count() or 1
-    T = inputs.temperature_ladder(T_MIN, T_MAX, N_REP)
-    ens = oracle.OracleEnsemble(inputs.random_coil(N_BEADS, N_REP, 1, 0), T, 1, delta=0.3,
-                                recompute_every=1000, n_bins=4096, threads=threads)
+    ens = _oracle_sample(w, threads)
     t0 = time.perf_counter()
     ens.run(2, 1)
     per_sweep = (time.perf_counter() - t0) / 2
@@ -154,8 +180,8 @@ def cpu_baseline(target_s: float = 15.0, threads: int | None = None):
     t0 = time.perf_counter()
     ens.run(n, 1)
     dt = time.perf_counter() - t0
-    return {"value": N_REP * N_BEADS * n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"ensemble seed 1 of {N_ENS} (N={N_BEADS}, {N_REP} replicas), {n} sweeps after 2 warm-up "
+    return {"value": c["R"] * c["N"] * n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"ensemble seed 1 of {c['E']} (N={c['N']}, {c['R']} replicas), {n} sweeps after 2 warm-up "
                       f"sweeps, exchange every sweep, FP64 oracle with {threads} OpenMP threads; {dt:.1f} s"}
 
 
@@ -163,12 +189,10 @@ def run_reference(args):
     ws, rank, local = dist_env()
     if ws > 1 and rank != 0:
         return 0
-    import oracle
-    from paper_1107_3490_gb300 import inputs
+    w = args.workload if args.workload in PLAIN else "long"
+    c = PLAIN[w]
     threads = os.cpu_count() or 1
-    T = inputs.temperature_ladder(T_MIN, T_MAX, N_REP)
-    ens = oracle.OracleEnsemble(inputs.random_coil(N_BEADS, N_REP, 1, 0), T, 1, delta=0.3,
-                                recompute_every=1000, n_bins=4096, threads=threads)
+    ens = _oracle_sample(w, threads)
     t0 = time.perf_counter()
     ens.run(2, 1)
     per_sweep = (time.perf_counter() - t0) / 2
@@ -181,14 +205,14 @@ def run_reference(args):
         t0 = time.perf_counter()
         ens.run(sweeps, 1)
         times.append(time.perf_counter() - t0)
-    upd = N_REP * N_BEADS * sweeps
+    upd = c["R"] * c["N"] * sweeps
     value = upd * len(times) / sum(times)
-    sample = (f"each step: {sweeps} sweeps of ensemble seed 1 (N={N_BEADS}, {N_REP} replicas), "
+    sample = (f"each step: {sweeps} sweeps of ensemble seed 1 (N={c['N']}, {c['R']} replicas), "
               f"exchange every sweep, FP64 oracle, {threads} OpenMP threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "reference_sample": sample},
+            "data": "synthetic", "config": {"workload": workload_text(w), "reference_sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -197,6 +221,8 @@ def run_reference(args):
 
 def run_gpu(args):
     import torch
+    w = args.workload
+    c = PLAIN[w]
     ws, rank, local = dist_env()
     if not torch.cuda.is_available():
         print(json.dumps({"error": "no CUDA device"}))
@@ -208,7 +234,7 @@ def run_gpu(args):
 
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     stream = torch.cuda.Stream(device=dev)
-    made = ensemble_params(rank)
+    made = ensemble_params(rank, w)
     h = pt.pt_create_batch([p for p, _ in made], stream.cuda_stream)
     if args.kernel >= 0:
         pt.pt_set_sweep_kernel(h, args.kernel)
@@ -248,7 +274,7 @@ def run_gpu(args):
     pt.pt_sync(h)
     local_ms = sum(step_ms)
     total_ms = reduce_max(local_ms, dist, dev)
-    value = updates_per_step() * ws * args.steps / (total_ms / 1e3)
+    value = updates_per_step(w) * ws * args.steps / (total_ms / 1e3)
     clocks = clk.summary()
 
     # ---- end to end through the C-ABI with host buffers: restore the state from pinned host
@@ -265,15 +291,15 @@ def run_gpu(args):
         pt.pt_sweep(h, SWEEPS_PER_STEP, 1)
         pt.pt_checkpoint_into(h, host)
     e2e_s = reduce_max(time.perf_counter() - t0, dist, dev)
-    e2e = {"value": updates_per_step() * ws * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": updates_per_step(w) * ws * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     # ---- roofline of the dominant kernel (the sweep): plain FP32 ALU work
-    pairs_per_launch = N_ENS * N_REP * N_BEADS * 2 * (N_BEADS - 1)  # one sweep per launch
+    pairs_per_launch = c["E"] * c["R"] * c["N"] * 2 * (c["N"] - 1)  # pair evaluations per sweep
     achieved = pairs_per_launch * FLOPS_PER_PAIR / (kernel_ms / 1e3) / 1e12
     peak = fp32_peak_tflops(num_sms, 2070.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": TRAFFIC_BYTES.get((KERNEL_NAMES[kernel], lmode)), "traffic_unit": "bytes per sweep",
+                "traffic": TRAFFIC_BYTES.get((w, KERNEL_NAMES[kernel], lmode)), "traffic_unit": "bytes per sweep",
                 "kernel": KERNEL_NAMES[kernel],
                 "kernel_ms_per_sweep": kernel_ms, "launches_sampled": kernel_n,
                 "launch_mode": "persistent (exchange in kernel)" if lmode == 1 else "graph per sweep",
@@ -292,17 +318,14 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": f"ensembles per GPU, {ws} GPU(s), no collective",
+            "config": {"workload": workload_text(w), "name": c["label"],
+                       "parallelism": f"ensembles per GPU, {ws} GPU(s), no collective",
                        "l2": "256 MB buffer written between timed steps (outside the per-step events)",
-                       "sweep_kernel": {0: "warp per replica", 1: "lookahead groups of 8 moves",
-                                        2: "team of warps per replica", 3: "warp per move of a group",
-                                        4: "warp per replica, chain in registers, deferred double-float",
-                                        5: "CTA per replica, one warp per move of a group, chain in registers"}[kernel],
-                       "pair_evals_per_s": value * 2 * (N_BEADS - 1)},
+                       "sweep_kernel": KERNEL_DESC[kernel], "pair_evals_per_s": value * 2 * (c["N"] - 1)},
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "clocks": clocks}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -490,7 +513,7 @@ def run_reweight(args):
     import numpy as np
     import oracle.wham as W
     from paper_1107_3490_gb300 import inputs, pt
-    R, N, nb = N_REP, N_BEADS, 4096
+    R, N, nb = 64, 100, 4096
     T = inputs.temperature_ladder(T_MIN, T_MAX, R)
     e_min, e_max = -8.0 * N, 2.0 * N
     p, keep = pt.make_params(N, T, 1, init_positions=inputs.random_coil(N, R, 1), n_bins=nb, n_therm=2000)
@@ -627,16 +650,19 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", choices=["plain", "batched", "served", "paper", "reweight", "table"], default="plain",
-                    help="plain: the benchmark line; batched / served: the uneven-ensemble and job-stream forms; "
+    ap.add_argument("--workload", choices=["long", "paper-scale", "batched", "served", "paper", "reweight", "table"],
+                    default="long",
+                    help="long: the benchmark line (N=1000 x 128 replicas); paper-scale: N=100 x 64 replicas x 4 "
+                         "ensembles; batched / served: the uneven-ensemble and job-stream forms; "
                          "paper: the paper's S_p protocol; reweight: histogram reweighting time; "
                          "table: GPU and oracle rates of the five configurations")
     ap.add_argument("--jobs", type=int, default=200)
     ap.add_argument("--rate", type=float, default=40.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5],
+    ap.add_argument("--kernel", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6],
                     help="sweep kernel: -1 autotune (default), 0 warp per replica, 1 lookahead groups, "
-                         "2 team of warps, 3 warp per move of a group, 4 chain in registers, 5 groups of moves")
+                         "2 team of warps, 3 warp per move of a group, 4 chain in registers, 5 groups of moves, "
+                         "6 CTA-wide groups of moves")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -206,8 +206,10 @@ int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonde
  * the device memory, a latency-critical loop that cannot afford an allocation's implicit
  * synchronisation, or a plug-in environment where only the host application allocates.
  * The paper has no counterpart; it is the allocation-free twin of pt_energy_fp64.
- *   conf:  DEVICE (or managed) memory, [n_conf][N][3] float coordinates, caller-owned.
- *   out:   DEVICE (or managed) memory, [n_conf] doubles, caller-owned.
+ *   conf:  memory of the CURRENT device (or managed), [n_conf][N][3] float coordinates,
+ *          caller-owned.
+ *   out:   memory of the current device (or managed), [n_conf] doubles, caller-owned.
+ * A buffer in host memory or on another device is rejected with PT_EINVAL.
  *   stream: cudaStream_t to enqueue on (NULL: the default stream); the call is asynchronous.
  * The partial sums live in one fixed device array of PT_NOALLOC_SCRATCH_DOUBLES doubles
  * (1 MiB) compiled into the library: every GPU that loads the library keeps it until the

@@ -287,17 +287,18 @@ void drop_graph(pt_ctx* h) {
     h->graph1 = nullptr;
 }
 
-// Kernel choice before any tuning, from timings on GB300 (4 x 64 replicas up to N = 300,
-// 128 replicas above; us per sweep, kernels 0 / 4 / 5): N = 10: 16.7 / 15.6 / 18.7;
-// N = 30: 34.6 / 27.9 / 27.9; N = 60: 68.2 / 46.0 / 43.0; N = 1000: kernel 2 945, kernel 5
-// 658. The chain in registers of one warp wins for short chains, a CTA of warps each taking
-// one move of a group from about 40 beads to the register limit, the team kernel beyond.
+// Kernel choice before any tuning, from timings on GB300 (4 x 64 replicas up to N = 100,
+// 128 replicas above; us per sweep): N = 10: kernel 4 15.6 / kernel 5 18.7; N = 30: 27.9 /
+// 27.9; N = 100: kernel 5 60.7 / kernel 6 63.5; N = 300: 172 / 104; N = 1000: 656 / 323. The
+// chain in registers of one warp wins for short chains, a CTA of warps each taking one move
+// of a group up to about 150 beads, and the CTA-wide group kernel (up to 4096 beads) above;
+// the team kernel beyond.
 // Kernels with a persistent (cooperative) mode, and the longest chain each one holds.
 bool has_persistent(int v) { return v == kSweepReg || v == kSweepGrp || v == kSweepCta; }
 int variant_max_n(int v) { return v == kSweepCta ? kCtaMaxN : (v == kSweepReg || v == kSweepGrp) ? kRegMaxN : 1 << 30; }
 
 int default_variant(int nmax) {
-    return nmax <= 40 ? kSweepReg : nmax <= kRegMaxN ? kSweepGrp : kSweepTeam;
+    return nmax <= 40 ? kSweepReg : nmax <= 150 ? kSweepGrp : nmax <= kCtaMaxN ? kSweepCta : kSweepTeam;
 }
 
 pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {

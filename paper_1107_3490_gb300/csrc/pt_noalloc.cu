@@ -80,13 +80,14 @@ __global__ void k_energy_final_xyz(const double* __restrict__ scratch, int n_con
     out[c] = t;
 }
 
-bool on_device(const void* p) {
+// Device memory of the current device dev, or managed memory (reachable from every device).
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -101,11 +102,11 @@ extern "C" int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int 
         return set_error(PT_EINVAL,
                          "pt_energy_fp64_noalloc: n_conf x chunks(N) exceeds the fixed scratch of "
                          "PT_NOALLOC_SCRATCH_DOUBLES doubles; split the call");
-    if (!conf || !out || !on_device(conf) || !on_device(out))
-        return set_error(PT_EINVAL, "pt_energy_fp64_noalloc: conf and out must be device (or managed) memory");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(PT_ECUDA, "pt_energy_fp64_noalloc: cudaGetDevice failed");
+    if (!conf || !out || !on_device(conf, dev) || !on_device(out, dev))
+        return set_error(PT_EINVAL, "pt_energy_fp64_noalloc: conf and out must be memory of the current device (or managed)");
     if (dev < 0 || dev >= kMaxDevices) return set_error(PT_EINVAL, "pt_energy_fp64_noalloc: device index too large");
     double* scratch = nullptr;
     {

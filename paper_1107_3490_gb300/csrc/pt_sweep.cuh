@@ -210,10 +210,11 @@ __device__ __forceinline__ bool ensemble_exchange(const State& S, const EnsDev& 
 // recompute of Eq. 4, then the measurement into the replica's temperature slot (the
 // replica owns the slot until the next exchange, so plain read-modify-write is race-free)
 // and the move counters.
+// A caller that has done the recompute itself passes recompute = false.
 __device__ __forceinline__ void sweep_epilogue(const State& S, const EnsDev& ed, int g, int gs, int slot, int N,
                                                const float4* P, int lane, int64_t s, int nacc, bool logging,
-                                               double& E) {
-    if (ed.recompute_every > 0 && (s + 1) % ed.recompute_every == 0) {
+                                               double& E, bool recompute = true) {
+    if (recompute && ed.recompute_every > 0 && (s + 1) % ed.recompute_every == 0) {
         const double full = warp_full_energy(P, N, ed.lj_bonded, lane);
         if (lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
         E = full;

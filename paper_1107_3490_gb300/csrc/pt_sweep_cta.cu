@@ -153,6 +153,34 @@ __device__ __forceinline__ float pending_term(const float4* PE, int e) {
 
 // Fixed point of a deferred correction; a non-finite or huge one (the accurate value of a
 // term the FP32 bracket accepted cannot be) is reported as a broken state.
+// FP64 total energy (Eq. 4) of the chain in shared memory by the whole CTA (TC threads):
+// bead i's pairs with every j > i, rows dealt to the threads in turn, per-thread sums added
+// in a fixed order (the same result in every launch). Every thread calls it.
+template <int TC>
+__device__ double cta_full_energy(const float4* P, int N, int lj_bonded, int tid, double* wsd) {
+    double e = 0.0;
+    for (int i = tid; i < N; i += TC) {
+        const float4 pi = P[i];
+        for (int j = i + 1; j < N; ++j) {
+            const double r2 = r2_d(pi, P[j]);
+            if (j == i + 1) {
+                e += fene_d(r2);
+                if (lj_bonded) e += lj_mod_d(r2);
+            } else {
+                e += lj_mod_d(r2);
+            }
+        }
+    }
+    e = warp_sum_d(e);
+    if ((tid & 31) == 0) wsd[tid >> 5] = e;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll 1
+    for (int w = 0; w < TC / 32; ++w) t += wsd[w];
+    __syncthreads();
+    return t;
+}
+
 __device__ __forceinline__ long long to_fix(float c, int* err) {
     if (!(fabsf(c) < 1.0e6f)) {
         atomicOr(err, kErrNonFinite);
@@ -614,7 +642,13 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
             fixc = 0;
             E = ((E + (double)dsum.hi) + (double)dsum.lo) + (double)ft * kFixInv;
         }
-        if (ctl) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E);
+        if (ed.recompute_every > 0 && (s + 1) % ed.recompute_every == 0) {
+            // the periodic FP64 recompute of Eq. 4, by the whole CTA
+            const double full = cta_full_energy<T + 32>(P, N, ed.lj_bonded, tid, reinterpret_cast<double*>(WSL));
+            if (ctl && lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
+            E = full;
+        }
+        if (ctl) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E, false);
         if (S.xin && ed.exchange_every > 0 && ed.R > 1 && (s + 1) % ed.exchange_every == 0) {
             if (ctl) {
                 int sl = slot;

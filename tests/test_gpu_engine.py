@@ -6,16 +6,11 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import parity, stats
 from oracle import quadrature as Q
 from paper_1107_3490_gb300 import inputs, pt
 
 pytestmark = pytest.mark.gpu
-
-
-def _block_se(x, n_blocks=40):
-    x = np.asarray(x)
-    b = x[: len(x) // n_blocks * n_blocks].reshape(n_blocks, -1).mean(axis=1)
-    return b.std(ddof=1) / math.sqrt(n_blocks)
 
 
 @pytest.mark.parametrize("lj_bonded", [1, 0])
@@ -41,10 +36,12 @@ def test_dimer_mean_energy_matches_quadrature(lj_bonded):
         per_slot[s] = g["e"][s][rot]
         for t in np.nonzero(g["x"][s] == 1)[0]:
             rot[t], rot[t + 1] = rot[t + 1], rot[t]
-    for t in range(4):
-        m1 = Q.dimer_moments(T[t], lj_bonded)[0]
-        e = per_slot[:, t]
-        assert abs(e.mean() - m1) < 4 * _block_se(e) + 1e-4, (T[t], e.mean(), m1)
+    # <E> and C_V (Eq. 7) per slot from 40 blocks against the quadrature, within two
+    # standard errors (the rule of tests/stats.py)
+    c, s1, s2 = stats.blocks_from_series(per_slot, 40)
+    m, sm, cv, scv = stats.jackknife_mean_cv(c, s1, s2, 1.0 / T)
+    exact = np.array([Q.dimer_moments(t, lj_bonded) for t in T])
+    stats.agreement(np.concatenate([(m - exact[:, 0]) / sm, (cv - exact[:, 2]) / scv]), f"dimer lj_bonded={lj_bonded}")
 
 
 def test_exchange_slot_marginals_enumeration():
@@ -253,6 +250,7 @@ def test_the_move_log_does_not_change_the_chain(variant):
     T = inputs.temperature_ladder(0.2, 3.0, 12)
     x0 = inputs.random_coil(70, 12, 31)
     out = []
+    glog = None
     for log in (False, True):
         p, keep = pt.make_params(70, T, 31, init_positions=x0, n_bins=128, recompute_every=0)
         h = pt.pt_create_ex(p)
@@ -261,6 +259,8 @@ def test_the_move_log_does_not_change_the_chain(variant):
             if log:
                 pt.pt_set_debug_log(h, 0, 40)
             pt.pt_sweep(h, 40, 1)
+            if log:
+                glog = pt.pt_get_debug_log(h, 40)
             out.append(dict(pos=pt.pt_get_positions(h), rot=pt.pt_get_permutation(h), E=pt.pt_energies(h),
                             hist=pt.pt_histograms(h), acc=pt.pt_acceptance(h)))
         finally:
@@ -270,8 +270,13 @@ def test_the_move_log_does_not_change_the_chain(variant):
     assert np.array_equal(a["hist"], b["hist"])
     if variant in (4, 5, 6):
         # with the log on, accepted dE values are refined at once instead of at the end of
-        # the sweep (and kernels 5 and 6 end groups differently): equal within the rounding
-        np.testing.assert_allclose(a["E"], b["E"], rtol=0, atol=1e-5)
+        # the sweep: each run's tracked energy lies within the summed per-move tolerance
+        # 1e-6 + 1e-5 |dE| of its accepted moves (their logged values), so the two within twice it
+        de = glog["de"].astype(np.float64).reshape(40, 12, 70)
+        acc = glog["acc"].reshape(40, 12, 70).astype(bool) & np.isfinite(de)
+        tol_rep = np.where(acc, parity.tol(de), 0.0).sum(axis=(0, 2))
+        bound = 2.0 * tol_rep[a["rot"]] + 1e-9  # by temperature slot
+        assert np.all(np.abs(a["E"] - b["E"]) <= bound), (np.abs(a["E"] - b["E"]), bound)
     else:
         assert np.array_equal(a["E"], b["E"])
     for x, y in zip(a["acc"], b["acc"]):

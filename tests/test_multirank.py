@@ -21,11 +21,12 @@ def _worker(rank, world, port, out):
                       LOCAL_RANK=str(rank))
     import bench
     dist = bench.init_dist(world, "gloo")
-    made = bench.ensemble_params(rank)
-    seeds = [int(p.seed) for p, _ in made]
-    ids = [int(p.ensemble_id) for p, _ in made]
+    res = []
+    for w in ("long", "paper-scale"):
+        made = bench.ensemble_params(rank, w)
+        res.append(([int(p.seed) for p, _ in made], [int(p.ensemble_id) for p, _ in made]))
     t = bench.reduce_max(1.0 + rank, dist)
-    out.put((rank, seeds, ids, t))
+    out.put((rank, res, t))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -47,7 +48,9 @@ def test_two_ranks_shard_ensembles_and_take_max_time():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    (r0, s0, i0, t0), (r1, s1, i1, t1) = res
-    assert set(s0).isdisjoint(s1) and set(i0).isdisjoint(i1)
-    assert s0 == [1, 2, 3, 4] and s1 == [5, 6, 7, 8]
+    (r0, w0, t0), (r1, w1, t1) = res
+    for (s0, i0), (s1, i1) in zip(w0, w1):
+        assert set(s0).isdisjoint(s1) and set(i0).isdisjoint(i1)
+    assert w0[0][0] == [1] and w1[0][0] == [2]  # long chains: one ensemble per rank
+    assert w0[1][0] == [1, 2, 3, 4] and w1[1][0] == [5, 6, 7, 8]  # paper-scale: four per rank
     assert t0 == t1 == 2.0

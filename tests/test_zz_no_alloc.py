@@ -9,6 +9,7 @@ collected last so that a failure here does not hide any other test's result.
 import numpy as np
 import pytest
 
+import oracle
 from paper_1107_3490_gb300 import inputs, pt
 
 pytestmark = pytest.mark.gpu
@@ -31,11 +32,19 @@ def test_noalloc_matches_allocating_entry_point_twice(N, n_conf, lj_bonded):
     ref = _reference(x, lj_bonded)
     conf = torch.from_numpy(x).cuda()            # the caller's device buffers
     stream = torch.cuda.current_stream().cuda_stream
-    for _ in range(2):                            # two calls in a row share the array
-        out = torch.full((n_conf,), float("nan"), dtype=torch.float64, device="cuda")
-        pt.pt_energy_fp64_noalloc(conf.data_ptr(), N, n_conf, lj_bonded, out.data_ptr(), stream)
+    orc = np.array([oracle.full_energy(x[c], lj_bonded) for c in range(n_conf)])  # Eq. 4 in FP64
+    outs = [torch.full((n_conf,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    free_before = None
+    for k in range(2):                            # two calls in a row share the array
+        pt.pt_energy_fp64_noalloc(conf.data_ptr(), N, n_conf, lj_bonded, outs[k].data_ptr(), stream)
         torch.cuda.synchronize()
-        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-10)
+        if k == 0:
+            free_before = torch.cuda.mem_get_info()[0]
+        np.testing.assert_allclose(outs[k].cpu().numpy(), ref, rtol=1e-12, atol=1e-10)
+        np.testing.assert_allclose(outs[k].cpu().numpy(), orc, rtol=1e-11, atol=1e-10)
+    # the call after the first (which looked up the array's address) takes no device memory
+    assert torch.cuda.mem_get_info()[0] == free_before
 
 
 def test_noalloc_rejects_oversized_and_host_buffers():

@@ -191,26 +191,35 @@ __device__ __forceinline__ long long to_fix(float c, int* err) {
 
 }  // namespace
 
+// Control warps of a CTA with W row warps: one per SM sub-partition from 8 row warps on.
+template <int W>
+__host__ __device__ constexpr int ctl_warps() { return W >= 8 ? 4 : 1; }
+
 template <int W>
 __host__ __device__ constexpr size_t cta_fixed_bytes() {
     return (size_t)(2 * 32 * W) * sizeof(float4)            // D0, D1
-           + (size_t)(W + 1) * kG * 4 * sizeof(float4)      // per-warp move records
+           + (size_t)(W + ctl_warps<W>()) * kG * 4 * sizeof(float4)  // per-warp move records
            + (size_t)kG * kCxStride * sizeof(float4)        // corrections
+           + (size_t)kG * sizeof(float4)                    // bond terms
            + (size_t)pend_cap<W>() * 3 * sizeof(float4)      // deferred terms
            + (size_t)W * 32 * sizeof(float)                 // reduce-scatter sums
-           + (size_t)(W + 1) * (sizeof(long long) + sizeof(float)) + 16 + kG * sizeof(unsigned) + 64;
+           + (size_t)(W + ctl_warps<W>()) * (sizeof(long long) + sizeof(float)) + 16 + kG * sizeof(unsigned) + 64;
 }
 
-// Warps 0..W-1 hold the chain (T = 32 W threads, U beads each) and evaluate the rows; warp W
-// is the control warp: while the rows run it evaluates the group's bond terms and the
-// corrections of the group pairs that can interact, and after the first group barrier it
-// takes the decisions. One CTA of 8 + 1 warps per SM holds a 1000-bead replica.
+// Warps 0..W-1 hold the chain (T = 32 W threads, U beads each) and evaluate the rows; warps
+// W..W+NC-1 are control warps: while the rows run they evaluate the group's bond terms and
+// the corrections of the group pairs that can interact (one control warp per SM
+// sub-partition, so that no row warp shares its issue slots with more than its share), and
+// after the first group barrier control warp 0 takes the decisions. One CTA of 8 + 4 warps
+// per SM holds a 1000-bead replica.
 template <int U, int W>
-__global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(State S, int chunk) {
-    constexpr int T = 32 * W, V = U / 2;
+__global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_sweep_cta(State S, int chunk) {
+    constexpr int T = 32 * W, V = U / 2, NC = ctl_warps<W>(), TC = T + 32 * NC;
     extern __shared__ float4 smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool ctl = warp == W;
+    const bool ctl = warp >= W;          // a control warp
+    const bool ctl0 = warp == W;         // the deciding control warp
+    const int cw = warp - W;
     const int g = blockIdx.x;
     if (g >= S.n_reps) return;  // whole CTA
     const RepDev rd = S.reps[g];
@@ -230,17 +239,18 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
     float4* P = smem;                              // [nmax] the chain
     float4* D0 = P + S.nmax;                       // [T] batch move: bead, displacement
     float4* D1 = D0 + T;                           // [T] batch move: theta, -, -, run length
-    float4* GMall = D1 + T;                        // [W + 1][kG][4] per-warp group records
-    float4* CX = GMall + (W + 1) * kG * 4;         // [kG][kCxStride] corrections (value, bound, flags)
-    float4* PE = CX + kG * kCxStride;              // [kPendCta][3] deferred accurate terms
+    float4* GMall = D1 + T;                        // [W + NC][kG][4] per-warp group records
+    float4* CX = GMall + (W + NC) * kG * 4;        // [kG][kCxStride] corrections (value, bound, flags)
+    float4* BND = CX + kG * kCxStride;             // [kG] bond terms of the group's moves (value, bound, flags)
+    float4* PE = BND + kG;                         // [kPendCta][3] deferred accurate terms
     float* RED = reinterpret_cast<float*>(PE + 3 * kPendCta);       // [W][32] warp sums
-    long long* WSL = reinterpret_cast<long long*>(RED + W * 32);    // [W + 1]
-    float* WS = reinterpret_cast<float*>(WSL + W + 1);               // [W + 1]
-    int* CNT = reinterpret_cast<int*>(WS + W + 1);  // [0] pending, [1] new slot, [2] accepted, [3] decided
+    long long* WSL = reinterpret_cast<long long*>(RED + W * 32);    // [W + NC]
+    float* WS = reinterpret_cast<float*>(WSL + W + NC);              // [W + NC]
+    int* CNT = reinterpret_cast<int*>(WS + W + NC);  // [0] pending, [1] new slot, [2] accepted, [3] decided
     unsigned* NEARM = reinterpret_cast<unsigned*>(CNT + 4);          // [kG] pairs with a correction
     float4* GM = GMall + warp * kG * 4;
 
-    for (int i = tid; i < N; i += T + 32) {
+    for (int i = tid; i < N; i += TC) {
         float4 q = S.pos[rd.pos_off + i];
         q.w = 0.f;
         P[i] = q;
@@ -283,7 +293,7 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
     // Deferred terms of every thread, summed now (CTA-wide; the caller is uniform).
     auto flush = [&]() {
         const int n = min(CNT[0], kPendCta);
-        for (int e = tid; e < n; e += T + 32) fixc += to_fix(pending_term(PE, e), S.err);
+        for (int e = tid; e < n; e += TC) fixc += to_fix(pending_term(PE, e), S.err);
         __syncthreads();
         if (tid == 0) CNT[0] = 0;
         __syncthreads();
@@ -373,9 +383,7 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
                     GM[4 * lane + 3] = make_float4(__int_as_float(0xfffd), 0.f, 0.f, 0.f);
                 }
                 __syncwarp();
-                unsigned stb = 0u;      // row threads: moves with a steep pair among this thread's slots
-                float bt = 0.f, be = 0.f;  // control warp, lane i: the bond terms of move i
-                unsigned bf = 0u;
+                unsigned stb = 0u;  // row threads: moves with a steep pair among this thread's slots
                 if (!ctl) {
                     // ---- the row of every group move over this thread's slots: values and
                     // bounds, in branch-free blocks of kMB moves so that their chains interleave
@@ -429,12 +437,12 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
                     }
                     RED[warp * 32 + lane] = reduce_scatter32(v, lane);
                 } else {
-                    // ---- control warp: the bond terms of the group's moves (lane 2i + side), then
-                    // the corrections of the pairs that can interact
+                    // ---- control warps: the bond terms of the group's moves (moves i = cw mod NC,
+                    // lane 2 j + side), then the corrections of the pairs that can interact
                     {
                         float t = 0.f, e = 0.f;
                         unsigned f = 0u;
-                        const int i = lane >> 1;
+                        const int i = cw + NC * (lane >> 1);
                         if (i < w) {
                             const int k = rec_k(i), j = (lane & 1) ? k + 1 : k - 1;
                             if (j >= 0 && j < N) {
@@ -444,16 +452,14 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
                                 f = bond_flags(x);
                             }
                         }
-                        // side 0 (lane 2i) + side 1 (lane 2i + 1), then to lane i
+                        // side 0 (lane 2 j) + side 1 (lane 2 j + 1)
                         t = __fadd_rn(t, __shfl_down_sync(kFull, t, 1));
                         e = __fadd_rn(e, __shfl_down_sync(kFull, e, 1));
                         f |= __shfl_down_sync(kFull, f, 1);
-                        bt = __shfl_sync(kFull, t, (2 * lane) & 31);
-                        be = __shfl_sync(kFull, e, (2 * lane) & 31);
-                        bf = __shfl_sync(kFull, f, (2 * lane) & 31);
+                        if (!(lane & 1) && i < w) BND[i] = make_float4(t, e, __uint_as_float(f), 0.f);
                     }
                     const int npairs = w * (w - 1) / 2;
-                    for (int pi = lane; pi < npairs; pi += 32) {
+                    for (int pi = cw + NC * lane; pi < npairs; pi += 32 * NC) {
                         int i, l;
                         tri_pair(pi, i, l);
                         const float4 ra = GM[4 * i], rb = GM[4 * i + 1], la = GM[4 * l], lb = GM[4 * l + 1];
@@ -475,14 +481,15 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
                 // whole CTA (thread 0's count may miss terms filed by warps still finishing the last
                 // group; the next group catches them, and a full list takes terms at once).
                 if (__syncthreads_or(tid == 0 && CNT[0] > kPendCta / 2)) flush();
-                // ---- control warp: totals in warp order, brackets, decisions, accepted values and
-                // the chain in shared memory
+                // ---- control warp 0: totals in warp order, brackets, decisions, accepted values
+                // and the chain in shared memory
                 unsigned am = 0u;    // control warp: accepted moves, decided moves, value of move
                 int nd0 = 0;         // lane, and the bond partners of an accepted move lane
                 float vi = 0.f;
                 bool acc_i = false;
                 float4 qm = make_float4(0.f, 0.f, 0.f, 0.f), qp = qm;
-                if (ctl) {
+                unsigned bf = 0u;
+                if (ctl0) {
                     float tot = 0.f;
 #pragma unroll
                     for (int w2 = 0; w2 < W; ++w2) tot = __fadd_rn(tot, RED[w2 * 32 + lane]);
@@ -491,6 +498,9 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
                     unsigned nm = 0u;
                     if (lane < w) {
                         th = GM[4 * lane + 3].y;
+                        const float4 bd = BND[lane];
+                        const float bt = bd.x, be = bd.y;
+                        bf = __float_as_uint(bd.z);
                         part = __fadd_rn(tot, bt);
                         const float bab = fabsf(bt) < kInf ? fabsf(bt) : 0.f;
                         const float el = __fmaf_ru(__fmul_ru(2.f * kDeltaRow, kSumInfl), ebt,
@@ -522,7 +532,7 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
                     }
                 }
                 __syncthreads();  // the second group barrier: decisions and the chain are out
-                if (ctl) {
+                if (ctl0) {
                     if (!logging && nd0 > 0) {
                         for (unsigned m = am; m; m &= m - 1) {
                             dsum = df_add(dsum, df{__shfl_sync(kFull, vi, __ffs(m) - 1), 0.f});
@@ -576,12 +586,12 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
                     __syncthreads();
                     float v0 = 0.f;
 #pragma unroll
-                    for (int w2 = 0; w2 < W; ++w2) v0 = __fadd_rn(v0, WS[w2]);
+                    for (int w2 = 0; w2 < W; ++w2) v0 = __fadd_rn(v0, WS[w2]);  // the row warps' shares
                     if (nd == 0) {
                         amask = v0 < th0 ? 1u : 0u;  // NaN and +inf reject
                         nd = 1;
                     }
-                    if (ctl) {
+                    if (ctl0) {
                         if (amask & 1u) {
                             dsum = df_add(dsum, df{v0, 0.f});
                             ++nacc;
@@ -637,20 +647,20 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
             __syncthreads();
             long long ft = 0;
 #pragma unroll
-            for (int w2 = 0; w2 <= W; ++w2) ft += WSL[w2];
+            for (int w2 = 0; w2 < W + NC; ++w2) ft += WSL[w2];
             __syncthreads();
             fixc = 0;
             E = ((E + (double)dsum.hi) + (double)dsum.lo) + (double)ft * kFixInv;
         }
         if (ed.recompute_every > 0 && (s + 1) % ed.recompute_every == 0) {
             // the periodic FP64 recompute of Eq. 4, by the whole CTA
-            const double full = cta_full_energy<T + 32>(P, N, ed.lj_bonded, tid, reinterpret_cast<double*>(WSL));
-            if (ctl && lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
+            const double full = cta_full_energy<TC>(P, N, ed.lj_bonded, tid, reinterpret_cast<double*>(WSL));
+            if (ctl0 && lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
             E = full;
         }
-        if (ctl) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E, false);
+        if (ctl0) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E, false);
         if (S.xin && ed.exchange_every > 0 && ed.R > 1 && (s + 1) % ed.exchange_every == 0) {
-            if (ctl) {
+            if (ctl0) {
                 int sl = slot;
                 const bool ok = ensemble_exchange(S, ed, rd.ens, g, rd.r, E, s + 1, xr, sl, lane);
                 if (lane == 0) CNT[1] = ok ? sl : -1;
@@ -670,7 +680,7 @@ __global__ void __launch_bounds__(32 * (W + 1), W >= 8 ? 1 : 2) k_sweep_cta(Stat
     }
     __syncthreads();
     for (int i = tid; i < N; i += T + 32) S.pos[rd.pos_off + i] = P[i];
-    if (ctl && lane == 0) {
+    if (ctl0 && lane == 0) {
         S.E[g] = E;
         S.rep_sweep[g] = s_end;
         if (S.xin) {
@@ -715,6 +725,12 @@ int cta_warps(int nmax) {
     return w;
 }
 
+// Threads of a CTA: the row warps and the control warps.
+static int cta_threads(int nmax) {
+    const int w = cta_warps(nmax);
+    return 32 * (w + (w >= 8 ? 4 : 1));
+}
+
 // The kernel of a shape, as a function pointer (nullptr: no such instantiation).
 static const void* cta_kernel(int nmax) {
     int u, w;
@@ -742,14 +758,14 @@ cudaError_t launch_sweep_cta(const State& s, int chunk, cudaStream_t st) {
     State sc = s;
     sc.xin = 0;
     void* args[] = {&sc, &chunk};
-    return cudaLaunchKernel(f, dim3(s.n_reps), dim3(32 * (cta_warps(s.nmax) + 1)), args, cta_smem_bytes(s.nmax), st);
+    return cudaLaunchKernel(f, dim3(s.n_reps), dim3(cta_threads(s.nmax)), args, cta_smem_bytes(s.nmax), st);
 }
 
 bool cta_coop_fits(const State& s, int nmax, int num_sms) {
     const void* f = cta_kernel(nmax);
     if (!f || nmax > kCtaMaxN) return false;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 32 * (cta_warps(nmax) + 1), cta_smem_bytes(nmax)) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, cta_threads(nmax), cta_smem_bytes(nmax)) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -762,7 +778,7 @@ cudaError_t launch_sweep_cta_coop(const State& s, int chunk, cudaStream_t st) {
     State sc = s;
     sc.xin = 1;
     void* args[] = {&sc, &chunk};
-    return cudaLaunchCooperativeKernel(f, dim3(s.n_reps), dim3(32 * (cta_warps(s.nmax) + 1)), args, cta_smem_bytes(s.nmax), st);
+    return cudaLaunchCooperativeKernel(f, dim3(s.n_reps), dim3(cta_threads(s.nmax)), args, cta_smem_bytes(s.nmax), st);
 }
 
 }  // namespace ptgb

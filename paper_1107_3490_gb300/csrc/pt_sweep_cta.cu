@@ -41,7 +41,8 @@ namespace ptgb {
 
 namespace {
 
-constexpr int kG = 16;                      // moves per group: 2 kG = 32 values per thread
+constexpr int kG = 16;                      // moves per group (16 or 32): halves of 16 moves
+constexpr int kH = kG / 16;                 // halves; each gives 32 values per thread to reduce
 constexpr int kCxStride = kG + 1;           // padded rows of the correction table
 constexpr int kMB = 4;                      // moves per branch-free block of the row pass
 constexpr float kDeltaRow = 4.0e-6f;        // 2e-6 for x plus 32 units of 2^-24 of rounding
@@ -71,6 +72,7 @@ __device__ __forceinline__ int excluded_slot(int k, int tid) {
 }
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ unsigned lowmask(int n) { return n >= 32 ? 0xffffffffu : (1u << n) - 1u; }
 __device__ __forceinline__ float min3f(float a, float b, float c) {
     float r;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -118,10 +120,10 @@ __device__ __forceinline__ void group_decide(int w, int lane, bool logging, floa
         done |= __ballot_sync(kFull, dec == 0 || dec == 1);
         accm |= __ballot_sync(kFull, dec == 1);
         if (und) nd = min(nd, __ffs(und) - 1);
-        const unsigned need = (1u << nd) - 1u;
+        const unsigned need = lowmask(nd);
         if ((done & need) == need) break;
     }
-    amask = accm & ((1u << nd) - 1u);
+    amask = accm & lowmask(nd);
 }
 
 // Sum over the warp of each of the 32 values v[0..31] of every lane; lane l returns the sum
@@ -202,7 +204,7 @@ __host__ __device__ constexpr size_t cta_fixed_bytes() {
            + (size_t)kG * kCxStride * sizeof(float4)        // corrections
            + (size_t)kG * sizeof(float4)                    // bond terms
            + (size_t)pend_cap<W>() * 3 * sizeof(float4)      // deferred terms
-           + (size_t)W * 32 * sizeof(float)                 // reduce-scatter sums
+           + (size_t)W * kH * 32 * sizeof(float)            // reduce-scatter sums
            + (size_t)(W + ctl_warps<W>()) * (sizeof(long long) + sizeof(float)) + 16 + kG * sizeof(unsigned) + 64;
 }
 
@@ -243,8 +245,8 @@ __global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_s
     float4* CX = GMall + (W + NC) * kG * 4;        // [kG][kCxStride] corrections (value, bound, flags)
     float4* BND = CX + kG * kCxStride;             // [kG] bond terms of the group's moves (value, bound, flags)
     float4* PE = BND + kG;                         // [kPendCta][3] deferred accurate terms
-    float* RED = reinterpret_cast<float*>(PE + 3 * kPendCta);       // [W][32] warp sums
-    long long* WSL = reinterpret_cast<long long*>(RED + W * 32);    // [W + NC]
+    float* RED = reinterpret_cast<float*>(PE + 3 * kPendCta);       // [W][kH][32] warp sums
+    long long* WSL = reinterpret_cast<long long*>(RED + W * kH * 32);  // [W + NC]
     float* WS = reinterpret_cast<float*>(WSL + W + NC);              // [W + NC]
     int* CNT = reinterpret_cast<int*>(WS + W + NC);  // [0] pending, [1] new slot, [2] accepted, [3] decided
     unsigned* NEARM = reinterpret_cast<unsigned*>(CNT + 4);          // [kG] pairs with a correction
@@ -386,63 +388,69 @@ __global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_s
                 unsigned stb = 0u;  // row threads: moves with a steep pair among this thread's slots
                 if (!ctl) {
                     // ---- the row of every group move over this thread's slots: values and
-                    // bounds, in branch-free blocks of kMB moves so that their chains interleave
-                    float acc[kG], eb[kG];
+                    // bounds, in branch-free blocks of kMB moves so that their chains interleave;
+                    // per half of 16 moves, warp sums of the 16 values and 16 bounds
 #pragma unroll
-                    for (int i = 0; i < kG; ++i) acc[i] = eb[i] = 0.f;
+                    for (int h = 0; h < kH; ++h) {
+                        float acc[16], eb[16];
 #pragma unroll
-                    for (int i0 = 0; i0 < kG; i0 += kMB) {
-                        if (i0 >= w) break;
+                        for (int i = 0; i < 16; ++i) acc[i] = eb[i] = 0.f;
 #pragma unroll
-                        for (int i = i0; i < i0 + kMB; ++i) {
-                            const float4 ra = GM[4 * i], rb = GM[4 * i + 1], rc = GM[4 * i + 2];
-                            const int k = __float_as_int(GM[4 * i + 3].x) & 0xffff;
-                            const float2 mpx = make_float2(ra.x, ra.y), mpy = make_float2(ra.z, ra.w),
-                                         mpz = make_float2(rb.x, rb.y);
-                            const float2 mnx = make_float2(rb.z, rb.w), mny = make_float2(rc.x, rc.y),
-                                         mnz = make_float2(rc.z, rc.w);
-                            const int uex = excluded_slot<T>(k, tid);
-                            float2 a2 = make_float2(0.f, 0.f), e2 = make_float2(0.f, 0.f);
-                            float mn = kRc2f;
+                        for (int i0 = 0; i0 < 16; i0 += kMB) {
+                            if (16 * h + i0 >= w) break;
 #pragma unroll
-                            for (int v = 0; v < V; ++v) {
-                                const float2 qx = make_float2(uex == 2 * v ? kFar : cx[v].x, uex == 2 * v + 1 ? kFar : cx[v].y);
-                                const float2 dxo = __fadd2_rn(qx, mpx), dyo = __fadd2_rn(cy[v], mpy), dzo = __fadd2_rn(cz[v], mpz);
-                                const float2 dxn = __fadd2_rn(qx, mnx), dyn = __fadd2_rn(cy[v], mny), dzn = __fadd2_rn(cz[v], mnz);
-                                const float2 r2o = __ffma2_rn(dzo, dzo, __ffma2_rn(dyo, dyo, __fmul2_rn(dxo, dxo)));
-                                const float2 r2n = __ffma2_rn(dzn, dzn, __ffma2_rn(dyn, dyn, __fmul2_rn(dxn, dxn)));
-                                const float co0 = fminf(r2o.x, kRc2f), co1 = fminf(r2o.y, kRc2f);
-                                const float cn0 = fminf(r2n.x, kRc2f), cn1 = fminf(r2n.y, kRc2f);
-                                mn = min3f(mn, min3f(co0, co1, cn0), cn1);
-                                const float2 io = make_float2(rcp_approx(co0), rcp_approx(co1));
-                                const float2 in = make_float2(rcp_approx(cn0), rcp_approx(cn1));
-                                const float2 xo = __fmul2_rn(__fmul2_rn(io, io), io), xn = __fmul2_rn(__fmul2_rn(in, in), in);
-                                const float2 d = __ffma2_rn(xo, f2(-1.f), xn);  // x_n - x_o, one rounding
-                                const float2 sx = __fadd2_rn(xn, xo);
-                                const float2 y = __ffma2_rn(f2(kAf), sx, f2(-kBf));
-                                a2 = __fadd2_rn(a2, __fmul2_rn(d, y));
-                                e2 = __ffma2_rn(sx, __ffma2_rn(f2(kAf), sx, f2(kBf)), e2);  // s (A s + B)
+                            for (int ib = i0; ib < i0 + kMB; ++ib) {
+                                const int i = 16 * h + ib;
+                                const float4 ra = GM[4 * i], rb = GM[4 * i + 1], rc = GM[4 * i + 2];
+                                const int k = __float_as_int(GM[4 * i + 3].x) & 0xffff;
+                                const float2 mpx = make_float2(ra.x, ra.y), mpy = make_float2(ra.z, ra.w),
+                                             mpz = make_float2(rb.x, rb.y);
+                                const float2 mnx = make_float2(rb.z, rb.w), mny = make_float2(rc.x, rc.y),
+                                             mnz = make_float2(rc.z, rc.w);
+                                const int uex = excluded_slot<T>(k, tid);
+                                float2 a2 = make_float2(0.f, 0.f), e2 = make_float2(0.f, 0.f);
+                                float mn = kRc2f;
+#pragma unroll
+                                for (int v = 0; v < V; ++v) {
+                                    const float2 qx = make_float2(uex == 2 * v ? kFar : cx[v].x, uex == 2 * v + 1 ? kFar : cx[v].y);
+                                    const float2 dxo = __fadd2_rn(qx, mpx), dyo = __fadd2_rn(cy[v], mpy), dzo = __fadd2_rn(cz[v], mpz);
+                                    const float2 dxn = __fadd2_rn(qx, mnx), dyn = __fadd2_rn(cy[v], mny), dzn = __fadd2_rn(cz[v], mnz);
+                                    const float2 r2o = __ffma2_rn(dzo, dzo, __ffma2_rn(dyo, dyo, __fmul2_rn(dxo, dxo)));
+                                    const float2 r2n = __ffma2_rn(dzn, dzn, __ffma2_rn(dyn, dyn, __fmul2_rn(dxn, dxn)));
+                                    const float co0 = fminf(r2o.x, kRc2f), co1 = fminf(r2o.y, kRc2f);
+                                    const float cn0 = fminf(r2n.x, kRc2f), cn1 = fminf(r2n.y, kRc2f);
+                                    mn = min3f(mn, min3f(co0, co1, cn0), cn1);
+                                    const float2 io = make_float2(rcp_approx(co0), rcp_approx(co1));
+                                    const float2 in = make_float2(rcp_approx(cn0), rcp_approx(cn1));
+                                    const float2 xo = __fmul2_rn(__fmul2_rn(io, io), io), xn = __fmul2_rn(__fmul2_rn(in, in), in);
+                                    const float2 d = __ffma2_rn(xo, f2(-1.f), xn);  // x_n - x_o, one rounding
+                                    const float2 sx = __fadd2_rn(xn, xo);
+                                    const float2 y = __ffma2_rn(f2(kAf), sx, f2(-kBf));
+                                    a2 = __fadd2_rn(a2, __fmul2_rn(d, y));
+                                    e2 = __ffma2_rn(sx, __ffma2_rn(f2(kAf), sx, f2(kBf)), e2);  // s (A s + B)
+                                }
+                                acc[ib] = __fadd_rn(a2.x, a2.y);
+                                eb[ib] = __fadd_rn(e2.x, e2.y);
+                                stb |= (mn < kSteepTeam2f ? 1u : 0u) << i;
                             }
-                            acc[i] = __fadd_rn(a2.x, a2.y);
-                            eb[i] = __fadd_rn(e2.x, e2.y);
-                            stb |= (mn < kSteepTeam2f ? 1u : 0u) << i;
                         }
-                    }
-                    // ---- warp sums of the group's values and bounds
-                    float v[32];
+                        float v[32];
 #pragma unroll
-                    for (int i = 0; i < kG; ++i) {
-                        v[i] = acc[i];
-                        v[kG + i] = eb[i];
+                        for (int i = 0; i < 16; ++i) {
+                            v[i] = acc[i];
+                            v[16 + i] = eb[i];
+                        }
+                        // lane l < 16: value of move 16 h + l; lane 16 + l: its bound
+                        RED[(warp * kH + h) * 32 + lane] = reduce_scatter32(v, lane);
                     }
-                    RED[warp * 32 + lane] = reduce_scatter32(v, lane);
                 } else {
                     // ---- control warps: the bond terms of the group's moves (moves i = cw mod NC,
                     // lane 2 j + side), then the corrections of the pairs that can interact
-                    {
+#pragma unroll
+                    for (int i0 = cw; i0 < kG; i0 += 16 * NC) {
                         float t = 0.f, e = 0.f;
                         unsigned f = 0u;
-                        const int i = cw + NC * (lane >> 1);
+                        const int i = i0 + NC * (lane >> 1);
                         if (i < w) {
                             const int k = rec_k(i), j = (lane & 1) ? k + 1 : k - 1;
                             if (j >= 0 && j < N) {
@@ -490,10 +498,16 @@ __global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_s
                 float4 qm = make_float4(0.f, 0.f, 0.f, 0.f), qp = qm;
                 unsigned bf = 0u;
                 if (ctl0) {
-                    float tot = 0.f;
+                    // lane i: the warps' sums of move i's values and bounds, in warp order
+                    float tot = 0.f, ebt = 0.f;
+                    if (lane < kG) {
+                        const int o = (lane >> 4) * 32 + (lane & 15);
 #pragma unroll
-                    for (int w2 = 0; w2 < W; ++w2) tot = __fadd_rn(tot, RED[w2 * 32 + lane]);
-                    const float ebt = __shfl_sync(kFull, tot, kG + (lane & (kG - 1)));
+                        for (int w2 = 0; w2 < W; ++w2) {
+                            tot = __fadd_rn(tot, RED[w2 * kH * 32 + o]);
+                            ebt = __fadd_rn(ebt, RED[w2 * kH * 32 + o + 16]);
+                        }
+                    }
                     float lo0 = kNaN, hi0 = kNaN, th = 0.f, part = 0.f;
                     unsigned nm = 0u;
                     if (lane < w) {
@@ -612,7 +626,7 @@ __global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_s
                 if (!ctl) {
                     // ---- steep row pairs of accepted moves with an FP32 value, deferred from this
                     // thread's slots (the chain at group start: no partner of such a move moved)
-                    unsigned todo = amask & stb & ((1u << nd) - 1u);
+                    unsigned todo = amask & stb & lowmask(nd);
                     if (need0) todo &= ~1u;
                     while (todo) {
                         const int i = __ffs(todo) - 1;

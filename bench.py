@@ -341,29 +341,40 @@ def _timed(fn):
 
 
 def run_batched(args):
-    """256 uneven ensembles (N log-uniform 20-500, 8-64 replicas, T 0.2-3.0) in one context
-    with one set of launches, against the plain form (each ensemble its own context, swept
-    one after another) on the first ensembles."""
+    """256 uneven ensembles (N log-uniform 20-500, 8-64 replicas, T 0.2-3.0) in one context,
+    against the plain form (each ensemble its own context, swept one after another) on the
+    first ensembles. The batched context runs the autotuned kernel and launch mode; kernel 4
+    is also timed in its work-list mode (every sweep of every replica in one launch per call)
+    and in per-sweep launches (a CUDA graph of sweep and exchange launches)."""
     import torch
     from paper_1107_3490_gb300 import inputs, pt
     specs = inputs.batched_ensembles(256, n_sweeps=5000)
     made = [pt.make_params(sp.n_beads, sp.temperatures(), sp.seed, ensemble_id=sp.ensemble_id, n_bins=1024)
             for sp in specs]
     steps_sweeps = 100
+    upd = sum(sp.n_beads * sp.n_replicas for sp in specs) * steps_sweeps
     h = pt.pt_create_batch([p for p, _ in made])
     kernel = pt.pt_autotune(h, 4)
-    for _ in range(args.warmup):
-        pt.pt_sweep(h, steps_sweeps, 1)
-    pt.pt_sync(h)
-    upd = sum(sp.n_beads * sp.n_replicas for sp in specs) * steps_sweeps
-    def timed_steps():
-        for _ in range(args.steps):
+    mode = pt.pt_get_launch_mode(h)
+
+    def rate():
+        for _ in range(args.warmup):
             pt.pt_sweep(h, steps_sweeps, 1)
         pt.pt_sync(h)
 
-    dt = _timed(timed_steps)
+        def timed_steps():
+            for _ in range(args.steps):
+                pt.pt_sweep(h, steps_sweeps, 1)
+            pt.pt_sync(h)
+        return upd * args.steps / _timed(timed_steps)
+
+    value = rate()
+    per_mode = {}
+    pt.pt_set_sweep_kernel(h, 4)
+    for m, name in ((2, "kernel 4, work list (one launch per call)"), (0, "kernel 4, per-sweep launches (CUDA graph)")):
+        pt.pt_set_launch_mode(h, m)
+        per_mode[name] = rate()
     pt.pt_destroy(h)
-    value = upd * args.steps / dt
     # plain form on a sample: one ensemble per context and per launch sequence
     sample = specs[:16]
     ctxs = []
@@ -380,11 +391,15 @@ def run_batched(args):
     plain = sum(sp.n_beads * sp.n_replicas for sp in sample) * steps_sweeps / t
     for c in ctxs:
         pt.pt_destroy(c)
+    modes = {0: "per-sweep launches", 1: "persistent (all replicas resident)", 2: "work list"}
+    launches = {0: 1 + -(-steps_sweeps // 32) * 64, 1: 3, 2: 2}[mode]  # per call
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "data": "synthetic", "dtype": "f32",
             "config": {"workload": "256 uneven PT ensembles: N log-uniform 20-500, replicas uniform 8-64, "
                                    "T geometric 0.2-3.0, exchange every sweep; one step = 100 sweeps of all",
-                       "sweep_kernel": KERNEL_NAMES[kernel], "replicas": sum(sp.n_replicas for sp in specs)},
+                       "sweep_kernel": KERNEL_NAMES[kernel], "launch_mode": modes[mode],
+                       "gpu_launches_per_step": launches, "replicas": sum(sp.n_replicas for sp in specs)},
+            "per_mode": per_mode,
             "plain_one_ensemble_per_launch": {"value": plain, "unit": UNIT, "sample": "first 16 ensembles, sequential"}}
     print(json.dumps(line), flush=True)
     return 0

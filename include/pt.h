@@ -253,15 +253,19 @@ int pt_get_sweep_kernel(const pt_ctx* h);
  * file, in that file; force = 1 measures again. *chosen (may be NULL) gets the kernel. */
 int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen);
 
-/* Launch mode. 1 (default): with kernel 4 or 5, when every replica's block can be resident
- * at once, a pt_sweep call with exchange_every >= 1 is one cooperative launch that runs all
- * its sweeps, each ensemble's exchange rounds done inside the kernel: the replicas of an
- * ensemble publish their energies under their temperature slots after the sweep an exchange
- * follows, and each replica waits for its partner of the round alone and takes its pair's
- * decision (Eq. 6). Every wait is bounded (about half a second); a wait that gives up makes
- * the call's later checks return PT_ETIMEOUT. 0: one
- * launch per sweep (replayed from a CUDA graph) and a separate exchange kernel. Both modes
- * run the same chain. pt_get_launch_mode returns the mode pt_sweep will actually use. */
+/* Launch mode. 1 (default): with kernel 4, 5 or 6, when every replica's block can be
+ * resident at once, a pt_sweep call with exchange_every >= 1 is one cooperative launch that
+ * runs all its sweeps, each ensemble's exchange rounds done inside the kernel: the replicas
+ * of an ensemble publish their energies under their temperature slots after the sweep an
+ * exchange follows, and each replica waits for its partner of the round alone and takes its
+ * pair's decision (Eq. 6). Every wait is bounded (about half a second); a wait that gives up
+ * makes the call's later checks return PT_ETIMEOUT. 2 (kernel 4): a work list, for contexts
+ * whose replicas cannot all be resident at once (many uneven ensembles): one launch per call
+ * whose warps take (replica, sweep) items in turn, longest chains first within a sweep; the
+ * last replica of an ensemble to finish a sweep takes the ensemble's exchange round and
+ * releases its next sweep (bounded waits as in mode 1). 0: one launch per sweep (replayed
+ * from a CUDA graph) and a separate exchange kernel. All modes run the same chain bit for
+ * bit. pt_get_launch_mode returns the mode pt_sweep will actually use. */
 int pt_set_launch_mode(pt_ctx* h, int mode);
 int pt_get_launch_mode(const pt_ctx* h);
 

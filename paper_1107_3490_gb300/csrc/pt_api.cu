@@ -75,6 +75,12 @@ struct pt_ctx {
     // the kernel (kernels 4 and 5, when the grid fits at once); 0 = per-sweep launches
     int launch_mode = 1;
     bool coop_ok = false;  // the current kernel's grid can be resident at once
+    // work-list launch (mode 2, kernel 4): item counter, per-ensemble release and arrival
+    // counts, replicas in hand-out order
+    unsigned long long* wl_next = nullptr;
+    int64_t* wl_ready = nullptr;
+    int* wl_arrive = nullptr;
+    int* wl_order = nullptr;
 };
 
 namespace {
@@ -197,10 +203,15 @@ void free_state(pt_ctx* h) {
     void* ptrs[] = {S.reps, S.ens, S.pos, S.E, S.temp_of_rep, S.rep_of_temp, S.Tf, S.beta, S.hist,
                     S.outl, S.mom, S.obs, S.obs_rg2_hist, S.obs_ree2_hist, S.mv_att, S.mv_acc, S.ex_att,
                     S.ex_acc, S.drift, S.rep_sweep, S.err, S.xstamp, S.xE, S.xhold, S.xrep, S.log_bead, S.log_de, S.log_theta, S.log_acc,
-                    S.log_e, S.log_x, h->scratch, h->conf_buf, h->eout_buf};
+                    S.log_e, S.log_x, h->scratch, h->conf_buf, h->eout_buf, h->wl_next, h->wl_ready, h->wl_arrive,
+                    h->wl_order};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     S = State{};
+    h->wl_next = nullptr;
+    h->wl_ready = nullptr;
+    h->wl_arrive = nullptr;
+    h->wl_order = nullptr;
     h->scratch = nullptr;
     h->conf_buf = nullptr;
     h->eout_buf = nullptr;
@@ -282,6 +293,20 @@ cudaError_t timed_sweep(pt_ctx* h, int chunk, bool persistent = false) {
     return e;
 }
 
+// The work-list launch, bracketed by timing events when timing is on.
+cudaError_t timed_worklist(pt_ctx* h, const WorkList& wl, int sweeps) {
+    auto go = [&]() { return launch_sweep_wl(h->S, wl, (int)h->ens.size(), h->num_sms, h->stream); };
+    if (h->tev.empty()) return go();
+    const int i = h->t_next;
+    cudaError_t e = cudaEventRecord(h->tev[2 * i], h->stream);
+    if (e == cudaSuccess) e = go();
+    if (e == cudaSuccess) e = cudaEventRecord(h->tev[2 * i + 1], h->stream);
+    h->t_sweeps[i] = sweeps;
+    h->t_next = (i + 1) % kTimingSlots;
+    h->t_count = std::min(h->t_count + 1, kTimingSlots);
+    return e;
+}
+
 void drop_graph(pt_ctx* h) {
     if (h->graph1) cudaGraphExecDestroy(h->graph1);
     h->graph1 = nullptr;
@@ -295,6 +320,8 @@ void drop_graph(pt_ctx* h) {
 // the team kernel beyond.
 // Kernels with a persistent (cooperative) mode, and the longest chain each one holds.
 bool has_persistent(int v) { return v == kSweepReg || v == kSweepGrp || v == kSweepCta; }
+// Kernels with the work-list launch (mode 2).
+bool has_worklist(int v) { return v == kSweepReg; }
 int variant_max_n(int v) { return v == kSweepCta ? kCtaMaxN : (v == kSweepReg || v == kSweepGrp) ? kRegMaxN : 1 << 30; }
 
 int default_variant(int nmax) {
@@ -396,6 +423,10 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     A(dalloc(&S.xE, 4 * G));
     A(dalloc(&S.xhold, (size_t)n_ens));
     A(dalloc(&S.xrep, 2 * G));
+    A(dalloc(&h->wl_next, 1));
+    A(dalloc(&h->wl_ready, (size_t)n_ens));
+    A(dalloc(&h->wl_arrive, (size_t)n_ens));
+    A(dalloc(&h->wl_order, G));
     if (a != cudaSuccess) {
         fail(a == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA, "device allocation: %s", cudaGetErrorString(a));
         pt_destroy(h);
@@ -438,6 +469,13 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     A(cudaMemcpy(S.temp_of_rep, ident.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice));
     A(cudaMemcpy(S.rep_of_temp, ident.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice));
     A(cudaMemcpy(S.Tf, Tf.data(), G * sizeof(float), cudaMemcpyHostToDevice));
+    {
+        // work-list hand-out order within a sweep: longest chains first (they finish last)
+        std::vector<int32_t> order(G);
+        for (int g = 0; g < G; ++g) order[g] = g;
+        std::stable_sort(order.begin(), order.end(), [&](int a_, int b_) { return h->reps[a_].N > h->reps[b_].N; });
+        A(cudaMemcpy(h->wl_order, order.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     A(cudaMemcpy(S.beta, beta.data(), G * sizeof(double), cudaMemcpyHostToDevice));
     if (a != cudaSuccess) {
         fail(PT_ECUDA, "upload: %s", cudaGetErrorString(a));
@@ -651,7 +689,20 @@ extern "C" int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every) {
                                                                                exchange_every);
     CK(h, cudaGetLastError());
     const int xe = exchange_every;
-    if (xe >= 1 && h->launch_mode == 1 && h->coop_ok) {
+    if (h->launch_mode == 2 && has_worklist(h->variant)) {
+        // work list: every sweep of every replica in one launch per chunk, the exchange rounds
+        // taken by the last replica of each ensemble to finish a sweep
+        if (h->t_graph) {
+            h->t_graph = false;
+            h->t_count = 0;
+            h->t_next = 0;
+        }
+        for (int64_t done = 0; done < n_sweeps; done += kMaxPersistent) {
+            const int64_t c = std::min<int64_t>(n_sweeps - done, kMaxPersistent);
+            WorkList wl{h->wl_next, h->wl_ready, h->wl_arrive, h->wl_order, h->done + done, (long long)(c * h->G)};
+            CK(h, timed_worklist(h, wl, (int)c));
+        }
+    } else if (xe >= 1 && h->launch_mode == 1 && h->coop_ok) {
         // persistent: each launch runs every ensemble up to its target (or chunk sweeps),
         // exchange rounds inside the kernel
         if (h->t_graph) {
@@ -711,6 +762,7 @@ extern "C" int pt_set_sweep_kernel(pt_ctx* h, int variant) {
         return fail(PT_EINVAL, "sweep kernel %d needs %zu bytes of shared memory per block for N=%d (the GPU has %d)",
                     variant, smem, h->nmax, h->smem_optin);
     CK(h, configure_sweep(h->nmax, warps, variant));
+    if (variant == kSweepReg) CK(h, configure_sweep_wl(h->nmax));
     h->variant = variant;
     h->warps = warps;
     h->coop_ok = sweep_coop_fits(h->S, h->nmax, variant, h->num_sms);
@@ -731,7 +783,7 @@ extern "C" int pt_test_stall_exchange(pt_ctx* h, int ensemble) {
 extern "C" int pt_set_launch_mode(pt_ctx* h, int mode) {
     int rc = check_usable(h);
     if (rc) return rc;
-    if (mode != 0 && mode != 1) return fail(PT_EINVAL, "launch mode must be 0 or 1");
+    if (mode < 0 || mode > 2) return fail(PT_EINVAL, "launch mode must be 0, 1 or 2");
     if ((rc = sync_and_check(h))) return rc;
     h->launch_mode = mode;
     return PT_OK;
@@ -739,6 +791,7 @@ extern "C" int pt_set_launch_mode(pt_ctx* h, int mode) {
 
 extern "C" int pt_get_launch_mode(const pt_ctx* h) {
     if (!h) return -1;
+    if (h->launch_mode == 2 && has_worklist(h->variant)) return 2;
     return (h->launch_mode == 1 && h->coop_ok && has_persistent(h->variant)) ? 1 : 0;
 }
 
@@ -804,8 +857,9 @@ extern "C" int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen) 
         if (sweep_smem_bytes(h->nmax, sweep_warps_per_block(h->nmax, h->G, h->num_sms, v), v) > (size_t)h->smem_optin)
             continue;
         if ((rc = pt_set_sweep_kernel(h, v))) break;
-        // kernels 4, 5 and 6 also in both launch modes (persistent where the grid fits)
-        for (int mode = 1; mode >= 0; --mode) {
+        // kernels 4, 5 and 6 also persistent (where the grid fits), kernel 4 also as a work list
+        for (int mode = 2; mode >= 0; --mode) {
+            if (mode == 2 && !has_worklist(v)) continue;
             if (mode == 1 && !(h->coop_ok && has_persistent(v))) continue;
             h->launch_mode = mode;
             if ((rc = pt_sweep(h, 2, 1))) break;  // warm-up (and graph capture)
@@ -1162,6 +1216,7 @@ extern "C" int pt_restore(pt_ctx* h, const void* buf, size_t size) {
     // the in-kernel exchange: no published round ahead of the restored one, no hold
     CK(h, cudaMemset(h->S.xstamp, 0, sizeof(unsigned long long) * (size_t)h->G));
     CK(h, cudaMemset(h->S.xhold, 0, sizeof(int) * h->ens.size()));
+    CK(h, cudaMemset(h->wl_arrive, 0, sizeof(int) * h->ens.size()));  // work list: no partial sweep
     h->done = (int64_t)hdr[2];
     return PT_OK;
 }

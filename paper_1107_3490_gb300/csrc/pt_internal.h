@@ -92,6 +92,18 @@ size_t reg_smem_bytes(int nmax);
 cudaError_t launch_sweep_reg(const State& s, int chunk, cudaStream_t st);
 bool reg_coop_fits(const State& s, int nmax, int num_sms);
 cudaError_t launch_sweep_reg_coop(const State& s, int chunk, cudaStream_t st);
+// Work-list launch of kernel 4 (launch mode 2): all sweeps of a call in one launch whose warps
+// take (replica, sweep) items in turn; see pt_sweep_reg.cu.
+struct WorkList {
+    unsigned long long* next;  // next item
+    int64_t* ready;            // [ensemble] sweeps its replicas may run up to (exclusive of the next)
+    int* arrive;               // [ensemble] replicas done with the ensemble's current sweep
+    const int* order;          // [replica] hand-out order within a sweep (longest chains first)
+    int64_t s0;                // sweep count of every ensemble at launch start
+    long long n_items;         // sweeps x replicas
+};
+cudaError_t launch_sweep_wl(const State& s, const WorkList& wl, int n_ens, int num_sms, cudaStream_t st);
+cudaError_t configure_sweep_wl(int nmax);
 int grp_warps(int nmax);
 size_t grp_smem_bytes(int nmax, int warps);
 cudaError_t configure_sweep_grp(int nmax);

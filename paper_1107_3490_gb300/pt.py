@@ -357,7 +357,8 @@ def pt_set_sweep_kernel(h, variant: int) -> None:
 
 
 def pt_set_launch_mode(h, mode: int) -> None:
-    """1: persistent launch with in-kernel exchange where possible (default); 0: per-sweep launches."""
+    """1: persistent launch with in-kernel exchange where possible (default); 2: work-list
+    launch (kernel 4); 0: per-sweep launches."""
     _ck(lib().pt_set_launch_mode(h, int(mode)))
 
 

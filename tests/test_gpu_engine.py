@@ -394,3 +394,60 @@ def test_exchange_barrier_wait_gives_up_and_the_context_recovers(variant):
     finally:
         pt.pt_destroy(h)
         pt.pt_destroy(ref)
+
+
+@pytest.mark.parametrize("xe", [1, 3])
+def test_worklist_launch_runs_the_same_chain(xe):
+    """Kernel 4's work-list launch (mode 2) against per-sweep launches (mode 0) on a batch of
+    uneven ensembles (N 20-150, 5-24 replicas): the same chain bit for bit, over several calls,
+    including the exchange labels, histograms, moments and counters."""
+    specs = [(20, 5, 1, 0), (150, 24, 2, 1), (47, 9, 3, 2), (96, 16, 4, 3), (33, 7, 5, 4)]
+    out = []
+    for mode in (2, 0):
+        made = [pt.make_params(N, inputs.temperature_ladder(0.2, 3.0, R), s, ensemble_id=e,
+                               init_positions=inputs.random_coil(N, R, s, e), n_bins=128, recompute_every=7)
+                for (N, R, s, e) in specs]
+        h = pt.pt_create_batch([p for p, _ in made])
+        try:
+            pt.pt_set_sweep_kernel(h, 4)
+            pt.pt_set_launch_mode(h, mode)
+            assert pt.pt_get_launch_mode(h) == mode
+            for n in (11, 1, 20):
+                pt.pt_sweep(h, n, xe)
+            out.append(_state(h) + (pt.pt_observables(h), [pt.pt_counters(h, e) for e in range(len(specs))]))
+        finally:
+            pt.pt_destroy(h)
+    a, b = out
+    _same(a[:5], b[:5])
+    for x, y in zip(a[5], b[5]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a[6], b[6]) and a[7] == b[7]
+
+
+def test_worklist_wait_gives_up_and_the_context_recovers():
+    """A work-list wait that cannot end (a hold on ensemble 0, made on the host): the call
+    reports PT_ETIMEOUT once, and after a restore the chain continues as an undisturbed one."""
+    import time
+    ref, h = _make(N=60, R=6, seed=31), _make(N=60, R=6, seed=31)
+    try:
+        for x in (ref, h):
+            pt.pt_set_sweep_kernel(x, 4)
+            pt.pt_set_launch_mode(x, 2)
+        pt.pt_sweep(h, 7, 1)
+        host = np.zeros(pt.pt_checkpoint_size(h), dtype=np.uint8)
+        n = pt.pt_checkpoint_into(h, host)
+        pt.pt_test_stall_exchange(h, 0)
+        t0 = time.time()
+        pt.pt_sweep(h, 10, 1)
+        with pytest.raises(pt.PtError) as err:
+            pt.pt_sync(h)
+        assert err.value.code == pt.PT_ETIMEOUT
+        assert time.time() - t0 < 60
+        pt.pt_sync(h)  # reported once
+        pt.pt_restore_from(h, host, n)
+        pt.pt_sweep(h, 10, 1)
+        pt.pt_sweep(ref, 17, 1)
+        _same(_state(h), _state(ref))
+    finally:
+        pt.pt_destroy(h)
+        pt.pt_destroy(ref)

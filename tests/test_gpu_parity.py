@@ -291,3 +291,34 @@ def test_long_chains_at_128_replicas_ten_sweeps(N):
           f"{rep.max_ratio:.3f}, divergence {rep.divergence}")
     if rep.divergence is None:
         _full_match(rep, out, orc, 10)
+
+
+def test_worklist_launch_against_the_oracle():
+    """Kernel 4's work-list launch on a batch of uneven ensembles, move for move against the
+    oracle for every ensemble over the first 20 sweeps."""
+    specs = [(25, 6, 3, 0), (90, 12, 4, 1), (41, 8, 5, 2)]
+    S = 20
+    made = [pt.make_params(N, inputs.temperature_ladder(0.2, 3.0, R), s, ensemble_id=e,
+                           init_positions=inputs.random_coil(N, R, s, e), n_bins=256, recompute_every=9)
+            for (N, R, s, e) in specs]
+    h = pt.pt_create_batch([p for p, _ in made])
+    try:
+        pt.pt_set_sweep_kernel(h, 4)
+        pt.pt_set_launch_mode(h, 2)
+        pt.pt_set_debug_log(h, 0, S)
+        pt.pt_sweep(h, S, 1)
+        g = pt.pt_get_debug_log(h, S)
+        G = pt.pt_total_replicas(h)
+    finally:
+        pt.pt_destroy(h)
+    ro = po = 0
+    for (N, R, s, e) in specs:
+        T = inputs.temperature_ladder(0.2, 3.0, R)
+        orc = oracle.OracleEnsemble(inputs.random_coil(N, R, s, e), T, s, ensemble_id=e, n_bins=256,
+                                    recompute_every=9, threads=8)
+        o = parity.oracle_log_with_labels(orc, S, 1)
+        rep = parity.compare(g, o, R, N, T, s, e, rep_offset=ro, pos_offset=po, n_reps_total=G)
+        assert rep.ok, (e, rep.failures)
+        assert rep.moves_compared > 0
+        ro += R
+        po += R * N

@@ -407,18 +407,21 @@ def run_batched(args):
 
 def run_served(args):
     """A Poisson stream of PT jobs (N log-uniform 20-1000, 16-128 replicas, budgets
-    log-uniform 100-1000 sweeps) through the continuous-batching server, against running
-    the same jobs one after another as plain contexts (on a sample)."""
+    log-uniform in [s_lo, s_hi] sweeps) through the continuous-batching server, against
+    running jobs of the same stream one after another as plain contexts (on a sample). The
+    configured stream has 2000 jobs with budgets 1e3-1e5 sweeps (about 8e14 pair
+    evaluations, tens of minutes of GPU time); the default here scales the budgets by 1/10
+    and the number of jobs by 1/2, and the line states the scale."""
     import threading
     from paper_1107_3490_gb300 import inputs, pt
     n_jobs = args.jobs
-    jobs = inputs.served_jobs(n_jobs, s_lo=100, s_hi=1000, rate_hz=args.rate)
+    jobs = inputs.served_jobs(n_jobs, s_lo=args.s_lo, s_hi=args.s_hi, rate_hz=args.rate)
     # clients arrive with their start conformations ready (made before the clock starts)
     made = [pt.make_params(j.n_beads, j.temperatures(), j.seed, ensemble_id=j.ensemble_id, n_bins=1024,
                            init_positions=pt.pt_make_coil(j.n_beads, j.n_replicas, j.seed, j.ensemble_id))
             for j in jobs]
-    cfg = pt.pt_server_config_init(1000, 6 << 30)
-    cfg.round_sweeps = 32
+    cfg = pt.pt_server_config_init(1000, 16 << 30)
+    cfg.round_sweeps = 64
     if args.kernel >= 0:
         cfg.sweep_kernel = args.kernel
     srv = pt.pt_server_create(cfg)
@@ -437,13 +440,14 @@ def run_served(args):
     th.join()
     lat = []
     for i, j in zip(ids, jobs):
-        pt.pt_server_wait(srv, i, 3600.0)
+        pt.pt_server_wait(srv, i, 7200.0)
         lat.append(pt.pt_server_result(srv, i, j.n_replicas, 1024)[3])
     makespan = time.perf_counter() - t_start
     upd = sum(j.n_beads * j.n_replicas * j.n_sweeps for j in jobs)
+    pairs = sum(j.n_beads * j.n_replicas * j.n_sweeps * 2 * (j.n_beads - 1) for j in jobs)
     pt.pt_server_destroy(srv)
-    # plain form: the first jobs one after another, each its own context
-    sample = list(zip(jobs, made))[:8]
+    # plain form: jobs of the stream one after another, each its own context (autotuned)
+    sample = list(zip(jobs, made))[:: max(1, n_jobs // 12)][:12]
     t = 0.0
     for j, (p, _) in sample:
         c = pt.pt_create_ex(p)
@@ -454,13 +458,18 @@ def run_served(args):
     lat = sorted(lat)
     line = {"metric": METRIC, "value": upd / makespan, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
             "data": "synthetic", "dtype": "f32",
-            "config": {"workload": f"{n_jobs} PT jobs, Poisson arrivals {args.rate}/s, N log-uniform 20-1000, "
-                                   "replicas uniform 16-128, budgets log-uniform 100-1000 sweeps, exchange every "
-                                   "sweep; server N_max 1000", "sweep_kernel": KERNEL_NAMES[args.kernel] if args.kernel >= 0 else "k_sweep_team (the server default)"},
+            "config": {"workload": f"{n_jobs} PT jobs, Poisson arrivals at {args.rate}/s, N log-uniform 20-1000, "
+                                   f"replicas uniform 16-128, budgets log-uniform {args.s_lo}-{args.s_hi} sweeps, "
+                                   "exchange every sweep; server N_max 1000",
+                       "scale_vs_configured": f"jobs {n_jobs}/2000, budgets {args.s_lo}-{args.s_hi} against 1e3-1e5",
+                       "arrival_rate_per_s": args.rate, "pair_evaluations": pairs, "updates": upd,
+                       "pool_kernels": "k_sweep_reg work list up to 320 beads, k_sweep_cta above"
+                       if args.kernel < 0 else KERNEL_NAMES[args.kernel]},
             "latency_s": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                           "max": lat[-1]},
             "makespan_s": makespan,
-            "plain_one_job_per_context": {"value": plain, "unit": UNIT, "sample": "first 8 jobs, sequential"}}
+            "plain_one_job_per_context": {"value": plain, "unit": UNIT,
+                                          "sample": f"{len(sample)} jobs spread over the stream, sequential, autotuned"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -671,8 +680,10 @@ def main(argv=None):
                          "ensembles; batched / served: the uneven-ensemble and job-stream forms; "
                          "paper: the paper's S_p protocol; reweight: histogram reweighting time; "
                          "table: GPU and oracle rates of the five configurations")
-    ap.add_argument("--jobs", type=int, default=200)
-    ap.add_argument("--rate", type=float, default=40.0)
+    ap.add_argument("--jobs", type=int, default=1000)
+    ap.add_argument("--rate", type=float, default=12.0)
+    ap.add_argument("--s-lo", dest="s_lo", type=int, default=100)
+    ap.add_argument("--s-hi", dest="s_hi", type=int, default=10000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5, 6],
                     help="sweep kernel: -1 autotune (default), 0 warp per replica, 1 lookahead groups, "

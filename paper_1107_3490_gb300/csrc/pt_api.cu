@@ -81,6 +81,7 @@ struct pt_ctx {
     int64_t* wl_ready = nullptr;
     int* wl_arrive = nullptr;
     int* wl_order = nullptr;
+    int64_t* wl_base = nullptr;
 };
 
 namespace {
@@ -204,7 +205,7 @@ void free_state(pt_ctx* h) {
                     S.outl, S.mom, S.obs, S.obs_rg2_hist, S.obs_ree2_hist, S.mv_att, S.mv_acc, S.ex_att,
                     S.ex_acc, S.drift, S.rep_sweep, S.err, S.xstamp, S.xE, S.xhold, S.xrep, S.log_bead, S.log_de, S.log_theta, S.log_acc,
                     S.log_e, S.log_x, h->scratch, h->conf_buf, h->eout_buf, h->wl_next, h->wl_ready, h->wl_arrive,
-                    h->wl_order};
+                    h->wl_order, h->wl_base};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     S = State{};
@@ -212,6 +213,7 @@ void free_state(pt_ctx* h) {
     h->wl_ready = nullptr;
     h->wl_arrive = nullptr;
     h->wl_order = nullptr;
+    h->wl_base = nullptr;
     h->scratch = nullptr;
     h->conf_buf = nullptr;
     h->eout_buf = nullptr;
@@ -295,7 +297,7 @@ cudaError_t timed_sweep(pt_ctx* h, int chunk, bool persistent = false) {
 
 // The work-list launch, bracketed by timing events when timing is on.
 cudaError_t timed_worklist(pt_ctx* h, const WorkList& wl, int sweeps) {
-    auto go = [&]() { return launch_sweep_wl(h->S, wl, (int)h->ens.size(), h->num_sms, h->stream); };
+    auto go = [&]() { return launch_sweep_wl(h->S, wl, h->num_sms, h->stream); };
     if (h->tev.empty()) return go();
     const int i = h->t_next;
     cudaError_t e = cudaEventRecord(h->tev[2 * i], h->stream);
@@ -427,6 +429,7 @@ pt_ctx* create_impl(int n_ens, const pt_params* params, void* stream) {
     A(dalloc(&h->wl_ready, (size_t)n_ens));
     A(dalloc(&h->wl_arrive, (size_t)n_ens));
     A(dalloc(&h->wl_order, G));
+    A(dalloc(&h->wl_base, (size_t)n_ens));
     if (a != cudaSuccess) {
         fail(a == cudaErrorMemoryAllocation ? PT_ENOMEM : PT_ECUDA, "device allocation: %s", cudaGetErrorString(a));
         pt_destroy(h);
@@ -699,7 +702,7 @@ extern "C" int pt_sweep(pt_ctx* h, int64_t n_sweeps, int exchange_every) {
         }
         for (int64_t done = 0; done < n_sweeps; done += kMaxPersistent) {
             const int64_t c = std::min<int64_t>(n_sweeps - done, kMaxPersistent);
-            WorkList wl{h->wl_next, h->wl_ready, h->wl_arrive, h->wl_order, h->done + done, (long long)(c * h->G)};
+            WorkList wl{h->wl_next, h->wl_ready, h->wl_arrive, h->wl_order, h->wl_base, (long long)(c * h->G)};
             CK(h, timed_worklist(h, wl, (int)c));
         }
     } else if (xe >= 1 && h->launch_mode == 1 && h->coop_ok) {

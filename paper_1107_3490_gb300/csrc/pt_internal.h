@@ -99,10 +99,11 @@ struct WorkList {
     int64_t* ready;            // [ensemble] sweeps its replicas may run up to (exclusive of the next)
     int* arrive;               // [ensemble] replicas done with the ensemble's current sweep
     const int* order;          // [replica] hand-out order within a sweep (longest chains first)
-    int64_t s0;                // sweep count of every ensemble at launch start
+    int64_t* base;             // [ensemble] its sweep count at launch start (set by the launch)
     long long n_items;         // sweeps x replicas
 };
-cudaError_t launch_sweep_wl(const State& s, const WorkList& wl, int n_ens, int num_sms, cudaStream_t st);
+// Every ensemble's replicas start at the sweep count of the ensemble's first replica.
+cudaError_t launch_sweep_wl(const State& s, const WorkList& wl, int num_sms, cudaStream_t st);
 cudaError_t configure_sweep_wl(int nmax);
 int grp_warps(int nmax);
 size_t grp_smem_bytes(int nmax, int warps);

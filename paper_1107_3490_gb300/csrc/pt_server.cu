@@ -83,6 +83,11 @@ struct Ranges {
 struct Pool {
     int nmax = 0, variant = 0, warps = 1, dummy = 0, n_jobs = 0;
     State S{};
+    // work-list launch (kernel 4): counters, hand-out order (rebuilt when the slots change)
+    unsigned long long* wl_next = nullptr;
+    int64_t *wl_ready = nullptr, *wl_base = nullptr;
+    int *wl_arrive = nullptr, *wl_order = nullptr;
+    bool order_dirty = true;
     Ranges reps, beads, bins;
     std::vector<int> free_ens;
     int ens_high = 0;  // one past the highest ensemble slot in use
@@ -135,7 +140,8 @@ cudaError_t dzero(T** p, size_t n) {
 void free_pool(Pool& P) {
     State& S = P.S;
     void* ptrs[] = {S.reps, S.ens, S.pos, S.E, S.temp_of_rep, S.rep_of_temp, S.Tf, S.beta, S.hist,
-                    S.outl, S.mom, S.mv_att, S.mv_acc, S.ex_att, S.ex_acc, S.drift, S.rep_sweep, S.err};
+                    S.outl, S.mom, S.mv_att, S.mv_acc, S.ex_att, S.ex_acc, S.drift, S.rep_sweep, S.err,
+                    S.xhold, P.wl_next, P.wl_ready, P.wl_base, P.wl_arrive, P.wl_order};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     S = State{};
@@ -182,17 +188,24 @@ cudaError_t make_pool(Pool& P, int nmax, int64_t reps, int64_t beads, int64_t bi
     A(dzero(&S.drift, G));
     A(dzero(&S.rep_sweep, G));
     A(dzero(&S.err, 1));
+    A(dzero(&S.xhold, NE));
+    A(dzero(&P.wl_next, 1));
+    A(dzero(&P.wl_ready, NE));
+    A(dzero(&P.wl_base, NE));
+    A(dzero(&P.wl_arrive, NE));
+    A(dzero(&P.wl_order, G));
     if (a == cudaSuccess) a = reset_slots(P, 0, (int64_t)G);
     P.reps = Ranges(reps);
     P.beads = Ranges(beads);
     P.bins = Ranges(bins);
     for (int e = jobs - 1; e >= 0; --e) P.free_ens.push_back(e);
-    // short chains: one warp per replica; longer: warp per move of a group
-    // A loaded server is throughput-bound (many replicas in flight), where the team kernel
-    // measured best (200 Poisson jobs, N 20-1000: 2.54e8 updates/s against 2.27e8-2.45e8
-    // for kernels 3-5, also the lowest p50 / p99 latency).
-    P.variant = variant >= 0 ? variant : kSweepTeam;
+    // A loaded pool holds many more replicas than can be resident at once. Up to 320 beads
+    // one warp per replica (kernel 4) in its work-list launch: one launch per round, warps
+    // taking (replica, sweep) items, so uneven chains keep every SM busy; above, the CTA-wide
+    // group kernel (6) per sweep, up to its 4096 beads; the team kernel beyond.
+    P.variant = variant >= 0 ? variant : nmax <= 320 ? kSweepReg : nmax <= kCtaMaxN ? kSweepCta : kSweepTeam;
     if ((P.variant == kSweepReg || P.variant == kSweepGrp) && nmax > kRegMaxN) P.variant = kSweepWpm;  // N <= 1024
+    if (P.variant == kSweepCta && nmax > kCtaMaxN) P.variant = kSweepTeam;
     P.warps = sweep_warps_per_block(nmax, (int)G, num_sms, P.variant);
     if (a == cudaSuccess) a = configure_sweep(nmax, P.warps, P.variant);
     return a;
@@ -208,10 +221,15 @@ void release(Pool& P, Job& j) {
     P.bins.give(j.hb, (int64_t)R * j.p.n_bins);
     P.free_ens.push_back(j.e);
     --P.n_jobs;
+    P.order_dirty = true;
 }
 
-// 1 admitted, 0 no room yet, -2 rejected (non-finite start energy), -1 CUDA failure.
-int admit(pt_server* s, Job& j) {
+// Admission, first half: take ranges of every kind in the job's pool and enqueue, on the
+// pool's stream, the copies of its descriptors, labels, temperatures and start
+// conformations, the clearing of its counters and the FP64 start energies (Eq. 4; the
+// partial sums use the job's histogram range as scratch, cleared after). 1 started, 0 no
+// room yet, -1 CUDA failure. admit_finish completes it once the stream has run.
+int admit_begin(pt_server* s, Job& j) {
     Pool& P = *s->pools[j.pool];
     const pt_params& p = j.p;
     const int R = p.n_replicas, N = p.N;
@@ -232,6 +250,7 @@ int admit(pt_server* s, Job& j) {
     const int e = P.free_ens.back();
     P.free_ens.pop_back();
     ++P.n_jobs;
+    P.order_dirty = true;
     j.e = e;
     j.rb = rb;
     j.pb = pb;
@@ -273,43 +292,52 @@ int admit(pt_server* s, Job& j) {
     std::vector<float4> x4((size_t)N * R);
     for (size_t i = 0; i < x4.size(); ++i) x4[i] = make_float4(j.x0[3 * i], j.x0[3 * i + 1], j.x0[3 * i + 2], 0.f);
     const size_t RR = (size_t)R;
-    cudaError_t c = cudaMemcpy(S.reps + rb, rd.data(), RR * sizeof(RepDev), cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.ens + e, &d, sizeof d, cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.temp_of_rep + rb, ident.data(), RR * 4, cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.rep_of_temp + rb, ident.data(), RR * 4, cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.Tf + rb, Tf.data(), RR * 4, cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.beta + rb, beta.data(), RR * 8, cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemcpy(S.pos + pb, x4.data(), x4.size() * sizeof(float4), cudaMemcpyHostToDevice);
-    if (c == cudaSuccess) c = cudaMemset(S.outl + 2 * rb, 0, 2 * RR * 8);
-    if (c == cudaSuccess) c = cudaMemset(S.mom + 3 * rb, 0, 3 * RR * 8);
-    if (c == cudaSuccess) c = cudaMemset(S.mv_att + rb, 0, RR * 8);
-    if (c == cudaSuccess) c = cudaMemset(S.mv_acc + rb, 0, RR * 8);
-    if (c == cudaSuccess) c = cudaMemset(S.ex_att + rb, 0, RR * 8);
-    if (c == cudaSuccess) c = cudaMemset(S.ex_acc + rb, 0, RR * 8);
-    if (c == cudaSuccess) c = cudaMemset(S.drift + rb, 0, RR * 8);
-    if (c == cudaSuccess) c = cudaMemset(S.rep_sweep + rb, 0, RR * 8);
-    // FP64 start energies (Eq. 4); the partial sums use the job's histogram range as
-    // scratch before it is cleared (submit checks it is large enough)
+    cudaStream_t st = P.stream;
+    // pageable sources: each copy has read its source when the call returns
+    cudaError_t c = cudaMemcpyAsync(S.reps + rb, rd.data(), RR * sizeof(RepDev), cudaMemcpyHostToDevice, st);
+    if (c == cudaSuccess) c = cudaMemcpyAsync(S.ens + e, &d, sizeof d, cudaMemcpyHostToDevice, st);
+    if (c == cudaSuccess) c = cudaMemcpyAsync(S.temp_of_rep + rb, ident.data(), RR * 4, cudaMemcpyHostToDevice, st);
+    if (c == cudaSuccess) c = cudaMemcpyAsync(S.rep_of_temp + rb, ident.data(), RR * 4, cudaMemcpyHostToDevice, st);
+    if (c == cudaSuccess) c = cudaMemcpyAsync(S.Tf + rb, Tf.data(), RR * 4, cudaMemcpyHostToDevice, st);
+    if (c == cudaSuccess) c = cudaMemcpyAsync(S.beta + rb, beta.data(), RR * 8, cudaMemcpyHostToDevice, st);
+    if (c == cudaSuccess) c = cudaMemcpyAsync(S.pos + pb, x4.data(), x4.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+    if (c == cudaSuccess) c = cudaMemsetAsync(S.outl + 2 * rb, 0, 2 * RR * 8, st);
+    if (c == cudaSuccess) c = cudaMemsetAsync(S.mom + 3 * rb, 0, 3 * RR * 8, st);
+    if (c == cudaSuccess) c = cudaMemsetAsync(S.mv_att + rb, 0, RR * 8, st);
+    if (c == cudaSuccess) c = cudaMemsetAsync(S.mv_acc + rb, 0, RR * 8, st);
+    if (c == cudaSuccess) c = cudaMemsetAsync(S.ex_att + rb, 0, RR * 8, st);
+    if (c == cudaSuccess) c = cudaMemsetAsync(S.ex_acc + rb, 0, RR * 8, st);
+    if (c == cudaSuccess) c = cudaMemsetAsync(S.drift + rb, 0, RR * 8, st);
+    if (c == cudaSuccess) c = cudaMemsetAsync(S.rep_sweep + rb, 0, RR * 8, st);
     const int nc = energy_chunks(N);
-    if (c == cudaSuccess)
-        c = launch_energy(S.pos, S.reps + rb, S.ens, 0, 1, R, S.E + rb, S.hist + hb, nc, P.stream);
-    if (c == cudaSuccess) c = cudaStreamSynchronize(P.stream);
-    if (c == cudaSuccess) c = cudaMemset(S.hist + hb, 0, RR * p.n_bins * 8);
-    std::vector<double> E(R);
-    if (c == cudaSuccess) c = cudaMemcpy(E.data(), S.E + rb, RR * 8, cudaMemcpyDeviceToHost);
+    if (c == cudaSuccess) c = launch_energy(S.pos, S.reps + rb, S.ens, 0, 1, R, S.E + rb, S.hist + hb, nc, st);
+    if (c == cudaSuccess) c = cudaMemsetAsync(S.hist + hb, 0, RR * p.n_bins * 8, st);
     if (c != cudaSuccess) {
+        s->error = PT_ECUDA;
+        return -1;
+    }
+    P.S.n_reps = (int)std::max<int64_t>(P.S.n_reps, rb + R);
+    P.ens_high = std::max(P.ens_high, e + 1);
+    P.S.n_ens = P.ens_high;
+    return 1;
+}
+
+// Admission, second half (the pool's stream has run): 1 admitted, -2 rejected (a
+// non-finite start energy: overlapping beads), -1 CUDA failure.
+int admit_finish(pt_server* s, Job& j) {
+    Pool& P = *s->pools[j.pool];
+    const int R = j.p.n_replicas;
+    std::vector<double> E(R);
+    if (cudaMemcpy(E.data(), P.S.E + j.rb, (size_t)R * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
         s->error = PT_ECUDA;
         return -1;
     }
     for (double v : E)
         if (!std::isfinite(v)) {
-            j.status = PT_EINVAL;  // overlapping start conformation
+            j.status = PT_EINVAL;
             release(P, j);
             return -2;
         }
-    P.S.n_reps = (int)std::max<int64_t>(P.S.n_reps, rb + R);
-    P.ens_high = std::max(P.ens_high, e + 1);
-    P.S.n_ens = P.ens_high;
     j.status = 1;
     return 1;
 }
@@ -336,19 +364,37 @@ int collect(Pool& P, Job& j) {
 // pools, and the job table is read and written under the lock).
 int round_locked(pt_server* s, std::unique_lock<std::mutex>& lk) {
     if (s->error) return s->error;
+    // admission: every queued job that fits starts (copies and energies enqueued), then one
+    // synchronisation per pool and the finiteness checks
+    std::vector<int64_t> started;
     for (auto it = s->queue.begin(); it != s->queue.end();) {
         Job& j = s->jobs[*it];
-        const int a = admit(s, j);
+        const int a = admit_begin(s, j);
         if (a == 1) {
-            s->running.push_back(j.id);
-            it = s->queue.erase(it);
-        } else if (a == -2) {
-            j.finished = Clock::now();
+            started.push_back(j.id);
             it = s->queue.erase(it);
         } else if (a < 0) {
             return s->error;
         } else {
             ++it;
+        }
+    }
+    if (!started.empty()) {
+        for (auto& pp : s->pools)
+            if (cudaStreamSynchronize(pp->stream) != cudaSuccess) {
+                s->error = PT_ECUDA;
+                return s->error;
+            }
+        for (int64_t id : started) {
+            Job& j = s->jobs[id];
+            const int a = admit_finish(s, j);
+            if (a == 1) {
+                s->running.push_back(id);
+            } else if (a == -2) {
+                j.finished = Clock::now();
+            } else {
+                return s->error;
+            }
         }
     }
     if (s->running.empty()) return 0;
@@ -359,12 +405,36 @@ int round_locked(pt_server* s, std::unique_lock<std::mutex>& lk) {
     }
     const int64_t n = std::min<int64_t>(todo, s->cfg.round_sweeps);
     const std::vector<int64_t> batch = s->running;
+    // work-list hand-out order of the pools whose slots changed: longest chains first
+    for (auto& pp : s->pools) {
+        Pool& P = *pp;
+        if (P.variant != kSweepReg || !P.order_dirty || P.S.n_reps == 0) continue;
+        std::vector<int32_t> order((size_t)P.S.n_reps), len((size_t)P.S.n_reps, 0);
+        for (int64_t id : s->running) {
+            const Job& j = s->jobs[id];
+            if (j.pool != (int)(&pp - &s->pools[0])) continue;
+            for (int r = 0; r < j.p.n_replicas; ++r) len[(size_t)(j.rb + r)] = j.p.N;
+        }
+        for (int g = 0; g < P.S.n_reps; ++g) order[(size_t)g] = g;
+        std::stable_sort(order.begin(), order.end(), [&](int a_, int b_) { return len[(size_t)a_] > len[(size_t)b_]; });
+        if (cudaMemcpy(P.wl_order, order.data(), order.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            s->error = PT_ECUDA;
+            return s->error;
+        }
+        P.order_dirty = false;
+    }
     lk.unlock();
-    // every pool with jobs on its own stream: the classes overlap on the device
+    // every pool with jobs on its own stream: the classes overlap on the device. Kernel 4
+    // pools run the whole round as one work-list launch, the others one launch per sweep.
     int gpu_err = 0;
     for (auto& pp : s->pools) {
         Pool& P = *pp;
         if (P.n_jobs == 0) continue;
+        if (P.variant == kSweepReg) {
+            WorkList wl{P.wl_next, P.wl_ready, P.wl_arrive, P.wl_order, P.wl_base, (long long)(n * P.S.n_reps)};
+            if (launch_sweep_wl(P.S, wl, s->num_sms, P.stream) != cudaSuccess) gpu_err = PT_ECUDA;
+            continue;
+        }
         for (int64_t i = 0; i < n && !gpu_err; ++i) {
             cudaError_t c = launch_sweep(P.S, 1, P.warps, P.variant, P.stream);
             if (c == cudaSuccess) c = launch_exchange(P.S, P.stream);
@@ -380,6 +450,8 @@ int round_locked(pt_server* s, std::unique_lock<std::mutex>& lk) {
             gpu_err = PT_ECUDA;
         else if (err & kErrNonFinite)
             gpu_err = PT_ESTATE;
+        else if (err & kErrTimeout)
+            gpu_err = PT_ETIMEOUT;
     }
     lk.lock();
     if (gpu_err) {
@@ -435,7 +507,7 @@ void worker_loop(pt_server* s) {
 }
 
 // Chain-length classes: (lower bound exclusive, upper bound inclusive].
-constexpr int kClassTop[] = {64, 256, PT_MAX_N};
+constexpr int kClassTop[] = {40, 150, 320, 1024, PT_MAX_N};
 
 int pool_of(const pt_server* s, int N) {
     for (size_t i = 0; i < s->pools.size(); ++i)

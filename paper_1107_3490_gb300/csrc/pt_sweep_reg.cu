@@ -337,9 +337,9 @@ __global__ void __maxnreg__(U >= 32 ? 248 : 168) k_sweep_wl(State S, WorkList wl
         it = __shfl_sync(kFull, it, 0);
         if ((long long)it >= wl.n_items) return;
         const int g = wl.order[it % (unsigned long long)S.n_reps];
-        const int64_t s = wl.s0 + (int64_t)(it / (unsigned long long)S.n_reps);
         const RepDev rd = S.reps[g];
         const EnsDev ed = S.ens[rd.ens];
+        const int64_t s = wl.base[rd.ens] + (int64_t)(it / (unsigned long long)S.n_reps);
         if (s >= ed.target) continue;
         // the ensemble's sweep s - 1 complete (and its exchange round done)
         int ok = 1;
@@ -399,9 +399,14 @@ __global__ void __maxnreg__(U >= 32 ? 248 : 168) k_sweep_wl(State S, WorkList wl
     }
 }
 
-__global__ void k_wl_start(WorkList wl, int n_ens, int64_t s0) {
+__global__ void k_wl_start(State S, WorkList wl) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n_ens) wl.ready[e] = s0;
+    if (e < S.n_ens) {
+        const EnsDev& ed = S.ens[e];
+        const int64_t s0 = ed.R > 0 ? S.rep_sweep[ed.rep_base] : 0;
+        wl.base[e] = s0;
+        wl.ready[e] = s0;
+    }
     if (e == 0) *wl.next = 0ull;
 }
 
@@ -415,8 +420,8 @@ static cudaError_t launch_wl(const State& s, const WorkList& wl, int num_sms, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_wl(const State& s, const WorkList& wl, int n_ens, int num_sms, cudaStream_t st) {
-    k_wl_start<<<(n_ens + 127) / 128, 128, 0, st>>>(wl, n_ens, wl.s0);
+cudaError_t launch_sweep_wl(const State& s, const WorkList& wl, int num_sms, cudaStream_t st) {
+    k_wl_start<<<(s.n_ens + 127) / 128, 128, 0, st>>>(s, wl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || wl.n_items <= 0) return e;
     const size_t smem = reg_smem_bytes(s.nmax);

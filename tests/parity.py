@@ -123,6 +123,22 @@ def compare(g: dict, o: dict, R: int, N: int, temps, seed: int, ens_id: int = 0,
     return rep
 
 
+def first_ambiguous_sweep(o):
+    """First sweep of an oracle log holding a move whose decision an exact-decision kernel
+    (4, 5, 6) may take differently: those take the exact decision wherever their rigorous
+    bracket decides, and otherwise decide on a double-float value within ~1e-7 of exact, so
+    besides the ulp by which the host and device logf may round theta differently, only
+    moves within 1e-6 of their threshold are ambiguous. None if there is no such move."""
+    de = o["de"]
+    th = o["theta"].astype(np.float64)
+    fin = np.isfinite(de)
+    margin = np.abs(np.where(fin, de, 0.0) - th)
+    slack = 1e-6 + 4.0 * np.spacing(o["theta"]).astype(np.float64)
+    amb = fin & (margin <= slack)
+    hit = np.nonzero(amb.reshape(amb.shape[0], -1).any(axis=1))[0]
+    return int(hit[0]) if hit.size else None
+
+
 def oracle_log_with_labels(ens, n_sweeps: int, exchange_every: int) -> dict:
     """Run the oracle n_sweeps, one sweep at a time, recording the labels before each."""
     log = ens.enable_log(n_sweeps)

@@ -9,7 +9,7 @@ last recompute, of the per-move tolerance 1e-6 + 1e-5 |dE|; exchange decisions (
 at the end, conformations, histograms and moments must agree. The context is swept one sweep
 per call (the same kernel, one persistent launch per sweep) so that the energies of every
 sweep can be read. The comparison stops at the first sweep in which the oracle log shows a
-decision the two sides may legitimately take differently (see _first_ambiguous_sweep).
+decision the two sides may legitimately take differently (parity.first_ambiguous_sweep).
 """
 import math
 
@@ -39,26 +39,10 @@ def _gpu_unlogged(made, variant, S, xe=1):
         pt.pt_destroy(h)
 
 
-def _first_ambiguous_sweep(o):
-    """First sweep of the oracle log holding a move whose decision the two sides may take
-    differently. Kernels 4-6 take the exact decision wherever their rigorous bracket decides,
-    and otherwise decide on a double-float value within ~1e-7 of exact; so besides the ulp
-    by which the host and device logf may round theta differently, only moves within 1e-6 of
-    their threshold are ambiguous (far inside the tolerance margin)."""
-    de = o["de"]
-    th = o["theta"].astype(np.float64)
-    fin = np.isfinite(de)
-    margin = np.abs(np.where(fin, de, 0.0) - th)
-    slack = 1e-6 + 4.0 * np.spacing(o["theta"]).astype(np.float64)
-    amb = fin & (margin <= slack)
-    hit = np.nonzero(amb.reshape(amb.shape[0], -1).any(axis=1))[0]
-    return int(hit[0]) if hit.size else None
-
-
 def _check_ensemble(g, o, orc, e, R, N, T, seed, S, recompute_every, n_bins, full_match_allowed):
     """Ensemble e of the GPU run (slots e R ... e R + R - 1) against its oracle log o."""
     sl = slice(e * R, (e + 1) * R)
-    stop = _first_ambiguous_sweep(o)
+    stop = parity.first_ambiguous_sweep(o)
     last = S if stop is None else stop  # sweeps [0, last) are unambiguous
     beta = 1.0 / np.asarray(T, dtype=np.float64)
     acc_tol = np.zeros(R)

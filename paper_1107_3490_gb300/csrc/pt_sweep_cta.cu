@@ -44,7 +44,7 @@ namespace {
 constexpr int kG = 16;                      // moves per group (16 or 32): halves of 16 moves
 constexpr int kH = kG / 16;                 // halves; each gives 32 values per thread to reduce
 constexpr int kCxStride = kG + 1;           // padded rows of the correction table
-constexpr int kMB = 4;                      // moves per branch-free block of the row pass
+constexpr int kMB = 2;                      // moves per branch-free block of the row pass
 constexpr float kDeltaRow = 4.0e-6f;        // 2e-6 for x plus 32 units of 2^-24 of rounding
 constexpr float kSumInfl = 1.0f + 64.f * 5.9604645e-08f;  // covers the round-to-nearest sums of w+
 // Deferred accurate terms held per CTA: 128 per warp; the list is flushed before a group

@@ -223,34 +223,39 @@ int pt_energy_fp64(pt_ctx* h, const float* conf, int N, int n_conf, int lj_bonde
 int pt_energy_fp64_noalloc(const float* conf, int N, int n_conf, int lj_bonded, double* out,
                            void* stream);
 
-/* Choose the sweep kernel (creation picks 4 up to 40 beads, 5 up to 1024 (4 up to 300 beads
- * when kernel 5's CTAs for every replica do not fit on the GPU at once), else 2):
+/* Choose the sweep kernel (creation picks 4 up to 40 beads, 5 up to 150, 6 up to 4096, else
+ * 2; 4 up to 300 beads when kernel 5's CTAs for every replica do not fit on the GPU at once):
  * 0 = one warp per replica, one move at a time;
  * 1 = one warp per replica, groups of up to 8 consecutive moves with distinct beads
  * evaluated together; 2 = a CTA of 1-8 warps per replica (by N), one move at a time;
  * 3 = a CTA of 2-8 warps per replica, each warp evaluating one move of a group of moves with
  * distinct beads; 4 = one warp per replica with the chain in registers (N_max <= 1024),
  * taking double-float work only where a decision or an accepted dE needs it; 5 = a CTA of
- * 4, 6 or 8 warps per replica (by N) with the chain in every warp's registers, each warp evaluating one
- * move of a group of consecutive moves on distinct beads, decisions taken in move order
- * (N_max <= 1024). Kernels 0-3 run the same chain, move for move, and differ only in the
- * summation order of dE. Kernels 4 and 5 take each Metropolis decision whose dE lies
- * outside its FP32 error bound of theta exactly, so they run that chain too except where a
- * dE falls within the parity tolerance of its threshold (and 4 and 5 run the same chain).
- * PT_EINVAL for an unknown kernel, kernel 4 or 5 with N_max > 1024, or a kernel whose
- * shared memory for N_max exceeds the GPU's per-block limit (kernel 3 above ~4500 beads);
- * the context stays usable. */
+ * 4, 6 or 8 warps per replica (by N) with the chain in every warp's registers, each warp
+ * evaluating one move of a group of consecutive moves on distinct beads, decisions taken in
+ * move order (N_max <= 1024); 6 = a CTA per replica whose row warps each hold a slice of the
+ * chain and evaluate every move of a group of up to 16 consecutive moves on distinct beads
+ * against it in packed FP32x2, with control warps for the bond terms, the corrections
+ * between group moves and the decisions (N_max <= 4096). Kernels 0-3 run the same chain,
+ * move for move, and differ only in the summation order of dE. Kernels 4, 5 and 6 take each
+ * Metropolis decision whose dE lies outside its rigorous FP32 error bound of theta exactly,
+ * so they run that chain too except where a dE falls within the parity tolerance of its
+ * threshold (and 4, 5 and 6 run the same chain). PT_EINVAL for an unknown kernel, kernel 4
+ * or 5 with N_max > 1024, kernel 6 with N_max > 4096, or a kernel whose shared memory for
+ * N_max exceeds the GPU's per-block limit (kernel 3 above ~4500 beads); the context stays
+ * usable. */
 int pt_set_sweep_kernel(pt_ctx* h, int variant);
 
 /* The kernel in use (creation picks one from the chain length; see pt_autotune). */
 int pt_get_sweep_kernel(const pt_ctx* h);
 
-/* Autotuner: time every sweep kernel (kernels 4 and 5 in both launch modes, see
- * pt_set_launch_mode) on this context for trial_sweeps sweeps (exchange every sweep) and
- * keep the fastest kernel and mode. The state is checkpointed before and restored after,
- * so the chain does not advance. The choice is cached per (GPU name, largest N, replica
- * count) in the process and, when the environment variable PTGB_AUTOTUNE_CACHE names a
- * file, in that file; force = 1 measures again. *chosen (may be NULL) gets the kernel. */
+/* Autotuner: time kernels 2, 4, 5 and 6 (4, 5 and 6 also persistent where every replica
+ * is resident, 4 also as a work list; see pt_set_launch_mode) on this context for
+ * trial_sweeps sweeps (exchange every sweep) and keep the fastest kernel and mode. The state
+ * is checkpointed before and restored after, so the chain does not advance. The choice is
+ * cached per (GPU name, largest N, replica count) in the process and, when the environment
+ * variable PTGB_AUTOTUNE_CACHE names a file, in that file; force = 1 measures again.
+ * *chosen (may be NULL) gets the kernel. */
 int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen);
 
 /* Launch mode. 1 (default): with kernel 4, 5 or 6, when every replica's block can be
@@ -317,9 +322,11 @@ typedef struct pt_server_config {
     int32_t job_capacity;     /* jobs resident at once                                    */
     int32_t round_sweeps;     /* sweeps per scheduling round (64)                         */
     int32_t threaded;         /* 1: a host thread runs the rounds; 0: pt_server_step      */
-    int32_t sweep_kernel;     /* -1: kernel 2 (team, best when loaded); else as           */
-                              /* pt_set_sweep_kernel (4 or 5 on a class above 1024 beads   */
-                              /* runs kernel 3)                                           */
+    int32_t sweep_kernel;     /* -1: per chain-length class (up to 40, 150, 320 beads:   */
+                              /* kernel 4 as a work list, one launch per round; up to 1024 */
+                              /* and beyond: kernel 6, above 4096 kernel 2); else as       */
+                              /* pt_set_sweep_kernel in every class (4 or 5 on a class     */
+                              /* above 1024 beads runs kernel 3)                          */
 } pt_server_config;
 
 /* Capacities for jobs of up to N_max beads in mem_budget_bytes of device memory. */

@@ -31,8 +31,10 @@
  * Precision: everything is FP64 except where the method itself fixes single precision:
  *   - coordinates are stored as float and the proposal is rounded to float;
  *   - the Metropolis threshold theta = -log(u) * T is formed in float (the paper runs
- *     all arithmetic in single precision, Sec. 3.4), so the accept decision
- *     dE < theta is taken against the same float threshold on every implementation.
+ *     all arithmetic in single precision, Sec. 3.4), so the accept decision dE < theta is
+ *     taken against a float threshold on every implementation. The host's logf and a
+ *     device's logf may round -log(u) one ulp apart, so two implementations' thresholds
+ *     can differ by that much; comparisons of decisions allow for it.
  * Compile with -O2 -ffp-contract=off and without -ffast-math.
  */
 #include <math.h>

@@ -854,7 +854,10 @@ extern "C" int pt_autotune(pt_ctx* h, int trial_sweeps, int force, int* chosen) 
     CK(h, cudaEventCreate(&b));
     int best = h->variant, best_mode = h->launch_mode;
     float best_ms = 1e30f;
-    const int variants[] = {kSweepSimple, kSweepLookahead, kSweepTeam, kSweepWpm, kSweepReg, kSweepGrp, kSweepCta};
+    // Kernels 0, 1 and 3 never win on GB300 (one move at a time with the double-float steep
+    // pairs inline, lookahead groups of one warp, a warp per move of a group): they stay
+    // selectable for cross-checks but are not timed here.
+    const int variants[] = {kSweepTeam, kSweepReg, kSweepGrp, kSweepCta};
     for (int v : variants) {
         if (h->nmax > variant_max_n(v)) continue;
         if (sweep_smem_bytes(h->nmax, sweep_warps_per_block(h->nmax, h->G, h->num_sms, v), v) > (size_t)h->smem_optin)

@@ -1,18 +1,21 @@
 // pt_server.cu -- continuous batching of parallel-tempering jobs.
 //
-// The server keeps device state in pools, one per chain-length class (up to 64 beads, up to
-// 256, up to N_max), each with fixed capacities (replica slots, beads, histogram bins, job
-// descriptors), its own sweep kernel shape and its own CUDA stream, so the classes run
+// The server keeps device state in pools, one per chain-length class (up to 40, 150, 320,
+// 1024 beads and up to N_max), each with fixed capacities (replica slots, beads, histogram
+// bins, job descriptors), its own sweep kernel and its own CUDA stream, so the classes run
 // concurrently on the device. A submitted job waits in a queue until first-fit ranges of
 // every kind are free in its class's pool; it is then admitted: its descriptors, start
-// conformations and labels are written into its ranges and its FP64 energies computed.
-// Every round launches, per pool, the sweep and exchange kernels once per sweep over the
-// occupied part of the pool (up to its high-water mark); each replica advances from its own
-// sweep counter to its job's budget, so jobs admitted at different times progress together.
-// After a round, finished jobs are copied out (energies by temperature slot, histograms,
-// moments) and their ranges freed, which lets queued jobs in. A job's arithmetic depends
-// only on its own descriptors and data and on its pool's kernel, so its result is the same
-// served alone and in any mix.
+// conformations and labels are written into its ranges and its FP64 energies computed (all
+// admissions of a round enqueued first, then one synchronisation per pool). Every round
+// advances every resident job by up to round_sweeps sweeps: pools of kernel 4 (up to 320
+// beads) as one work-list launch, whose warps take (replica, sweep) items and whose last
+// replica of a job to finish a sweep takes the job's exchange round; the other pools (kernel
+// 6) with the sweep and exchange kernels once per sweep over the occupied part of the pool.
+// Each replica advances from its own sweep counter to its job's budget, so jobs admitted at
+// different times progress together. After a round, finished jobs are copied out (energies
+// by temperature slot, histograms, moments) and their ranges freed, which lets queued jobs
+// in. A job's arithmetic depends only on its own descriptors and data and on its pool's
+// kernel, so its result is the same served alone and in any mix.
 #include <algorithm>
 #include <chrono>
 #include <cmath>

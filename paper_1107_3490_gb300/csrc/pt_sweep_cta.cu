@@ -193,9 +193,11 @@ __device__ __forceinline__ long long to_fix(float c, int* err) {
 
 }  // namespace
 
-// Control warps of a CTA with W row warps: one per SM sub-partition from 8 row warps on.
+// Control warps of a CTA with W row warps: one per SM sub-partition from 8 row warps on; 3
+// with 4 or 5 row warps and 2 with 2 (measured: N = 300 x 128 replicas 105 -> 90 us per
+// sweep with 3 control warps instead of 1; N = 100 x 256 replicas 64 -> 62 us with 2).
 template <int W>
-__host__ __device__ constexpr int ctl_warps() { return W >= 8 ? 4 : 1; }
+__host__ __device__ constexpr int ctl_warps() { return W >= 8 ? 4 : W >= 4 ? 3 : 2; }
 
 template <int W>
 __host__ __device__ constexpr size_t cta_fixed_bytes() {
@@ -742,7 +744,7 @@ int cta_warps(int nmax) {
 // Threads of a CTA: the row warps and the control warps.
 static int cta_threads(int nmax) {
     const int w = cta_warps(nmax);
-    return 32 * (w + (w >= 8 ? 4 : 1));
+    return 32 * (w + (w >= 8 ? 4 : w >= 4 ? 3 : 2));
 }
 
 // The kernel of a shape, as a function pointer (nullptr: no such instantiation).

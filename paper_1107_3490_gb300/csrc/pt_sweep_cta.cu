@@ -9,10 +9,11 @@
 // holds beads t, t + T, t + 2T, ... in registers and forms, for every move of the group, its
 // share of the O(N) row of Eqs. 1-2 (the moved bead against every bead but itself and its
 // two bonded neighbours) together with a rigorous bound on that share's rounding error. One
-// warp reduce-scatter gives, per warp, the sums of the group's values and bounds. After a
-// barrier, warp 0 adds the warps' sums, takes the group's decisions and writes the accepted
-// moves into the chain in shared memory; after a second barrier every thread reloads its
-// slots.
+// warp reduce-scatter gives, per warp, the sums of the group's values and bounds. Meanwhile
+// two to four control warps (beside the row warps) evaluate the group's bond terms and the
+// corrections between its moves. After a barrier, the first control warp adds the warps'
+// sums, takes the group's decisions and writes the accepted moves into the chain in shared
+// memory; after a second barrier every row thread reloads the slots an acceptance changed.
 //
 // Bound. A row term is t = x_n (A x_n - B) - x_o (A x_o - B), x = r^-6, computed as
 // (x_n - x_o)(A (x_n + x_o) - B). x carries a relative error of at most 17 units of 2^-24

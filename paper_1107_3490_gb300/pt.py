@@ -376,8 +376,8 @@ def pt_get_sweep_kernel(h) -> int:
 
 
 def pt_autotune(h, trial_sweeps: int = 8, force: bool = False) -> int:
-    """Time every sweep kernel (4 and 5 in both launch modes) on h, state restored
-    afterwards, and keep the fastest kernel and launch mode."""
+    """Time the candidate sweep kernels (2, 4, 5 and 6, each in the launch modes it supports)
+    on h, state restored afterwards, and keep the fastest kernel and launch mode."""
     v = ctypes.c_int(-1)
     _ck(lib().pt_autotune(h, int(trial_sweeps), int(bool(force)), ctypes.byref(v)))
     return v.value

@@ -6,13 +6,22 @@ samples are correlated, so the error of an estimate comes from the spread of its
 leave-one-block-out values over blocks longer than the correlation time.
 
 Agreement within two standard errors is read per point: z = (a - b) / sqrt(se_a^2 + se_b^2).
-With n points, about 4.6 % of them fall beyond two standard errors by chance alone, so the
-rule is that no more of them do than a Binomial(n, 0.0455) count exceeds with probability
-1e-3, that none lies beyond four standard errors, and that sum z^2 stays below the 0.999
-quantile of chi^2(n).
+With n independent points, about 4.6 % of them fall beyond two standard errors by chance
+alone, so the rule for independent points (`agreement`) is that no more of them do than a
+Binomial(n, 0.0455) count exceeds with probability 1e-3, that none lies beyond four standard
+errors, and that sum z^2 stays below the 0.999 quantile of chi^2(n).
+
+The points of a parallel-tempering run are not independent: replicas carry their state from
+one temperature to the next, so a run that sits low at one temperature sits low at its
+neighbours. For K independent runs a side (`permutation_agreement`) the same three
+statistics of the per-point Welch t are instead referred to their permutation distribution:
+under the null hypothesis (both sides sample the same chain from the same start) the 2K
+runs are exchangeable, whatever the correlations between points, so splitting them into two
+groups in every other way gives the exact law of each statistic.
 """
 from __future__ import annotations
 
+import itertools
 import math
 
 import numpy as np
@@ -90,3 +99,66 @@ def agreement(z, what=""):
     assert beyond2 <= kmax, msg
     assert chi2 <= chi2_max, msg
     return beyond2, chi2
+
+
+def _welch_t(sa, qa, ka, sb, qb, kb):
+    """Welch t per point from group sums sa, sb and sums of squares qa, qb (data centred)."""
+    ma, mb = sa / ka, sb / kb
+    va = np.maximum(qa - sa * ma, 0.0) / (ka - 1) / ka
+    vb = np.maximum(qb - sb * mb, 0.0) / (kb - 1) / kb
+    return (ma - mb) / np.sqrt(np.maximum(va + vb, 1e-300))
+
+
+def permutation_agreement(a, b, what="", alpha=1e-3, n_perm=20000, seed=0):
+    """Two-standard-error agreement of independent runs a [K_a, n] and b [K_b, n] (each row one
+    run, each column one point), calibrated by permutation of the runs. Statistics of the
+    per-point Welch t: the number of points beyond 2, max |t| and sum t^2. Each gets the
+    p-value of its observed value among all splits of the K_a + K_b runs into groups of K_a
+    and K_b (exhaustive up to n_perm splits, random beyond); the test fails when the smallest
+    p-value is below alpha / 3. Returns (points beyond 2, their fraction, p-values)."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    ka, kb = a.shape[0], b.shape[0]
+    x = np.concatenate([a, b], 0)
+    x = x - x.mean(0)
+    x2 = x * x
+    n = ka + kb
+    tot, tot2 = x.sum(0), x2.sum(0)
+
+    def stat(masks):
+        m = masks.astype(np.float64)
+        sa, qa = m @ x, m @ x2
+        t = _welch_t(sa, qa, ka, tot - sa, tot2 - qa, kb)
+        return np.stack([(np.abs(t) > 2.0).sum(1), np.abs(t).max(1), (t * t).sum(1)], 1)
+
+    obs_mask = np.zeros((1, n), dtype=bool)
+    obs_mask[0, :ka] = True
+    obs = stat(obs_mask)[0]
+    exhaustive = math.comb(n, ka) <= n_perm
+    if exhaustive:
+        it = itertools.combinations(range(n), ka)
+        total = math.comb(n, ka)
+    else:
+        rng = np.random.default_rng(seed)
+        total = n_perm
+    ge = np.zeros(3)
+    done = 0
+    while done < total:
+        bsz = min(2048, total - done)
+        masks = np.zeros((bsz, n), dtype=bool)
+        if exhaustive:
+            for r, c in enumerate(itertools.islice(it, bsz)):
+                masks[r, list(c)] = True
+        else:
+            for r in range(bsz):
+                masks[r, rng.permutation(n)[:ka]] = True
+        ge += (stat(masks) >= obs - 1e-9 * np.abs(obs) - 1e-12).sum(0)  # ties (a split and its mirror) count
+        done += bsz
+    pv = ge / total if exhaustive else (1.0 + ge) / (1.0 + total)
+    npts = a.shape[1]
+    msg = (f"{what}: {npts} points, {int(obs[0])} beyond 2 SE (p {pv[0]:.3g}), max |t| {obs[1]:.2f} "
+           f"(p {pv[1]:.3g}), sum t^2 {obs[2]:.1f} (p {pv[2]:.3g}); {'all' if exhaustive else total} splits of "
+           f"{ka} + {kb} runs")
+    print(msg)
+    assert np.all(np.isfinite(obs)), msg
+    assert pv.min() >= alpha / 3.0, msg
+    return int(obs[0]), obs[0] / npts, pv

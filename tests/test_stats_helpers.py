@@ -64,3 +64,59 @@ def test_welch_z_calibrated_with_few_runs():
     assert fails <= 9, fails
     with pytest.raises(AssertionError):
         stats.agreement(stats.welch_z(rng.normal(size=(8, 64)), rng.normal(size=(8, 64)) + 1.0))
+
+
+def _correlated_runs(rng, k, n, load):
+    """k runs of n points: a run-wide common factor (loading `load`) plus independent noise, as
+    the temperatures of one parallel-tempering run share the states of its replicas."""
+    return load * rng.normal(size=(k, 1)) + rng.normal(size=(k, n))
+
+
+def test_permutation_agreement_holds_its_level_under_correlated_points():
+    """Points sharing a run-wide factor: the rule for independent points fails far more often
+    than its nominal 0.1 % (sum z^2 is no chi^2 any more), the permutation test does not."""
+    import contextlib
+    import io
+    rng = np.random.default_rng(5)
+    chi2_fails = perm_fails = 0
+    for _ in range(60):
+        a, b = _correlated_runs(rng, 8, 64, 2.0), _correlated_runs(rng, 8, 64, 2.0)
+        with contextlib.redirect_stdout(io.StringIO()):
+            try:
+                stats.agreement(stats.welch_z(a, b))
+            except AssertionError:
+                chi2_fails += 1
+            try:
+                stats.permutation_agreement(a, b)
+            except AssertionError:
+                perm_fails += 1
+    assert chi2_fails >= 10, chi2_fails
+    assert perm_fails <= 1, perm_fails
+
+
+def test_permutation_agreement_catches_shifts():
+    """A shift of every point by one run standard deviation (independent points), a shift of
+    four times the common factor's spread (correlated points) and a single point shifted by
+    four run standard deviations are each caught."""
+    import contextlib
+    import io
+    rng = np.random.default_rng(9)
+    cases = [(rng.normal(size=(8, 64)), rng.normal(size=(8, 64)) + 1.0),
+             (_correlated_runs(rng, 8, 64, 1.0), _correlated_runs(rng, 8, 64, 1.0) + 4.0)]
+    b = rng.normal(size=(8, 64))
+    b[:, 17] += 4.0
+    cases.append((rng.normal(size=(8, 64)), b))
+    for a, b in cases:
+        with contextlib.redirect_stdout(io.StringIO()), pytest.raises(AssertionError):
+            stats.permutation_agreement(a, b)
+
+
+def test_permutation_p_values_are_exact_for_small_groups():
+    """4 + 4 runs: 70 splits, so the smallest possible p-value is 1/70 and the observed split
+    of identical groups has every statistic at its minimum (p = 1)."""
+    x = np.arange(8 * 3, dtype=float).reshape(8, 3) % 5
+    _, _, pv = stats.permutation_agreement(x[:4], x[:4] + 0.0, alpha=0.0)
+    assert np.all(pv == 1.0)
+    a = np.array([[0.0], [0.1], [0.2], [0.3]])
+    _, _, pv = stats.permutation_agreement(a, a + 10.0, alpha=0.0)
+    assert np.isclose(pv[1], 2 / 70) and np.isclose(pv[2], 2 / 70)

@@ -210,10 +210,11 @@ __device__ __forceinline__ bool ensemble_exchange(const State& S, const EnsDev& 
 // recompute of Eq. 4, then the measurement into the replica's temperature slot (the
 // replica owns the slot until the next exchange, so plain read-modify-write is race-free)
 // and the move counters.
-// A caller that has done the recompute itself passes recompute = false.
+// A caller that has done the recompute itself passes recompute = false; one that has taken
+// the shape observables itself passes them in shape (r_gyr^2, R_ee^2).
 __device__ __forceinline__ void sweep_epilogue(const State& S, const EnsDev& ed, int g, int gs, int slot, int N,
                                                const float4* P, int lane, int64_t s, int nacc, bool logging,
-                                               double& E, bool recompute = true) {
+                                               double& E, bool recompute = true, const double* shape = nullptr) {
     if (recompute && ed.recompute_every > 0 && (s + 1) % ed.recompute_every == 0) {
         const double full = warp_full_energy(P, N, ed.lj_bonded, lane);
         if (lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
@@ -221,7 +222,14 @@ __device__ __forceinline__ void sweep_epilogue(const State& S, const EnsDev& ed,
     }
     const bool measure = isfinite(E) && s >= ed.n_therm;
     double rg2 = 0.0, ree2 = 0.0;
-    if (measure && S.obs) warp_shape(P, N, lane, rg2, ree2);
+    if (measure && S.obs) {
+        if (shape) {
+            rg2 = shape[0];
+            ree2 = shape[1];
+        } else {
+            warp_shape(P, N, lane, rg2, ree2);
+        }
+    }
     if (lane == 0) {
         // Fire-and-forget atomic adds (no value returned, so the warp does not wait on L2).
         // The slot has a single writer until the next exchange and one thread's adds to an

@@ -184,6 +184,61 @@ __device__ double cta_full_energy(const float4* P, int N, int lj_bonded, int tid
     return t;
 }
 
+// Shape observables (Eq. 8) of the chain in shared memory by the whole CTA (TC threads), in
+// double-float on the FP32 pipe (the FP64 pipe is a small fraction of it): r_gyr^2 from the
+// centre of mass, R_ee^2 from the end beads; per-thread sums added in a fixed order. Every
+// thread calls it and gets the results.
+template <int TC>
+__device__ void cta_shape(const float4* P, int N, int tid, float2* wsf, double& rg2, double& ree2) {
+    constexpr int NW = TC / 32;
+    df cx = {0.f, 0.f}, cy = {0.f, 0.f}, cz = {0.f, 0.f};
+    for (int i = tid; i < N; i += TC) {
+        const float4 q = P[i];
+        cx = df_add(cx, df{q.x, 0.f});
+        cy = df_add(cy, df{q.y, 0.f});
+        cz = df_add(cz, df{q.z, 0.f});
+    }
+    cx = warp_sum_df(cx);
+    cy = warp_sum_df(cy);
+    cz = warp_sum_df(cz);
+    if ((tid & 31) == 0) {
+        wsf[3 * (tid >> 5)] = make_float2(cx.hi, cx.lo);
+        wsf[3 * (tid >> 5) + 1] = make_float2(cy.hi, cy.lo);
+        wsf[3 * (tid >> 5) + 2] = make_float2(cz.hi, cz.lo);
+    }
+    __syncthreads();
+    cx = cy = cz = df{0.f, 0.f};
+#pragma unroll 1
+    for (int w = 0; w < NW; ++w) {
+        cx = df_add(cx, df{wsf[3 * w].x, wsf[3 * w].y});
+        cy = df_add(cy, df{wsf[3 * w + 1].x, wsf[3 * w + 1].y});
+        cz = df_add(cz, df{wsf[3 * w + 2].x, wsf[3 * w + 2].y});
+    }
+    const df n = {(float)N, 0.f};  // exact: N < 2^24
+    cx = df_div(cx, n);
+    cy = df_div(cy, n);
+    cz = df_div(cz, n);
+    __syncthreads();
+    df g2 = {0.f, 0.f};
+    for (int i = tid; i < N; i += TC) {
+        const float4 q = P[i];
+        const df dx = df_sub(df{q.x, 0.f}, cx), dy = df_sub(df{q.y, 0.f}, cy), dz = df_sub(df{q.z, 0.f}, cz);
+        g2 = df_add(g2, df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz)));
+    }
+    g2 = warp_sum_df(g2);
+    if ((tid & 31) == 0) wsf[tid >> 5] = make_float2(g2.hi, g2.lo);
+    __syncthreads();
+    df t = {0.f, 0.f};
+#pragma unroll 1
+    for (int w = 0; w < NW; ++w) t = df_add(t, df{wsf[w].x, wsf[w].y});
+    __syncthreads();
+    const df r = df_div(t, n);
+    rg2 = (double)r.hi + (double)r.lo;
+    const float4 a = P[0];
+    const df e = r2_df(P[N - 1], make_float3(a.x, a.y, a.z));  // exact differences and squares
+    ree2 = (double)e.hi + (double)e.lo;
+}
+
 __device__ __forceinline__ long long to_fix(float c, int* err) {
     if (!(fabsf(c) < 1.0e6f)) {
         atomicOr(err, kErrNonFinite);
@@ -675,7 +730,10 @@ __global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_s
             if (ctl0 && lane == 0) S.drift[g] = fmax(S.drift[g], fabs(E - full));
             E = full;
         }
-        if (ctl0) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E, false);
+        // the shape observables by the whole CTA (D0 is free until the next batch)
+        double shape[2] = {0.0, 0.0};
+        if (S.obs && s >= ed.n_therm) cta_shape<TC>(P, N, tid, reinterpret_cast<float2*>(D0), shape[0], shape[1]);
+        if (ctl0) sweep_epilogue(S, ed, g, gs, slot, N, P, lane, s, nacc, logging, E, false, shape);
         if (S.xin && ed.exchange_every > 0 && ed.R > 1 && (s + 1) % ed.exchange_every == 0) {
             if (ctl0) {
                 int sl = slot;
@@ -696,7 +754,7 @@ __global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_s
         }
     }
     __syncthreads();
-    for (int i = tid; i < N; i += T + 32) S.pos[rd.pos_off + i] = P[i];
+    for (int i = tid; i < N; i += TC) S.pos[rd.pos_off + i] = P[i];
     if (ctl0 && lane == 0) {
         S.E[g] = E;
         S.rep_sweep[g] = s_end;

@@ -23,10 +23,12 @@ from tests import parity
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_unlogged(made, variant, S, xe=1):
+def _gpu_unlogged(made, variant, S, xe=1, mode=None):
     h = pt.pt_create_batch([p for p, _ in made])
     try:
         pt.pt_set_sweep_kernel(h, variant)
+        if mode is not None:
+            pt.pt_set_launch_mode(h, mode)
         es, rots = [], []
         for _ in range(S):
             pt.pt_sweep(h, 1, xe)
@@ -39,9 +41,13 @@ def _gpu_unlogged(made, variant, S, xe=1):
         pt.pt_destroy(h)
 
 
-def _check_ensemble(g, o, orc, e, R, N, T, seed, S, recompute_every, n_bins, full_match_allowed):
-    """Ensemble e of the GPU run (slots e R ... e R + R - 1) against its oracle log o."""
-    sl = slice(e * R, (e + 1) * R)
+def _check_ensemble(g, o, orc, e, R, N, T, seed, S, recompute_every, n_bins, full_match_allowed,
+                    rep_off=None, pos_off=None):
+    """Ensemble e of the GPU run (slots rep_off ... rep_off + R - 1, beads from pos_off; by
+    default those of equal ensembles before it) against its oracle log o."""
+    rep_off = e * R if rep_off is None else rep_off
+    pos_off = e * R * N if pos_off is None else pos_off
+    sl = slice(rep_off, rep_off + R)
     stop = parity.first_ambiguous_sweep(o)
     last = S if stop is None else stop  # sweeps [0, last) are unambiguous
     beta = 1.0 / np.asarray(T, dtype=np.float64)
@@ -74,7 +80,7 @@ def _check_ensemble(g, o, orc, e, R, N, T, seed, S, recompute_every, n_bins, ful
             return last, worst, False
     full = stop is None and full_match_allowed
     if full:
-        pos_g = g["pos"].reshape(-1, N, 3)[sl]
+        pos_g = g["pos"].reshape(-1, 3)[pos_off:pos_off + R * N].reshape(R, N, 3)
         assert np.array_equal(pos_g, orc.pos)
         hist = g["hist"].reshape(-1, n_bins)[sl]
         assert np.array_equal(hist.sum(1) + g["outl"][sl].sum(1), orc.hist.sum(1) + orc.outl.sum(1))
@@ -145,3 +151,40 @@ def test_recompute_resets_the_tolerance(variant):
     float coordinates on both sides (1e-12 relative); in between within the summed tolerance."""
     res = _run(60, 8, 30, [5], variant, recompute_every=7, n_bins=256)
     assert res[0][0] >= 7
+
+
+def test_batched_configuration_unlogged_sampled():
+    """The 256-ensemble batch of uneven chains (N 20-500, 8-64 replicas: 9,122 replicas) in the
+    launch the benchmark times (kernel 4, every sweep of every replica in one work-list launch
+    per call): 20 sweeps of the production path, and six of its ensembles (the longest and the
+    shortest chain, the most and the fewest replicas, two more) against the oracle."""
+    specs = inputs.batched_ensembles(256)
+    S, n_bins = 20, 1024
+    made = [pt.make_params(sp.n_beads, sp.temperatures(), sp.seed, ensemble_id=sp.ensemble_id,
+                           init_positions=inputs.random_coil(sp.n_beads, sp.n_replicas, sp.seed, sp.ensemble_id),
+                           n_bins=n_bins) for sp in specs]
+    g = _gpu_unlogged(made, 4, S, mode=2)
+    assert g["kernel"] == 4 and g["mode"] == 2
+    Ns = np.array([sp.n_beads for sp in specs])
+    Rs = np.array([sp.n_replicas for sp in specs])
+    pick = sorted({int(np.argmax(Ns)), int(np.argmin(Ns)), int(np.argmax(Rs)), int(np.argmin(Rs)), 77, 200})
+    rep_off = np.concatenate([[0], np.cumsum(Rs)])
+    pos_off = np.concatenate([[0], np.cumsum(Rs * Ns)])
+    for e in pick:
+        sp = specs[e]
+        T = sp.temperatures()
+        orc = oracle.OracleEnsemble(inputs.random_coil(sp.n_beads, sp.n_replicas, sp.seed, sp.ensemble_id), T, sp.seed,
+                                    ensemble_id=sp.ensemble_id, n_bins=n_bins, recompute_every=1000, threads=16)
+        log = orc.enable_log(S)
+        rb, rots, xrs = [], [], []
+        for _ in range(S):
+            rb.append(orc.rep_of_temp.copy())
+            xrs.append(orc.xround)
+            orc.run(1, 1)
+            rots.append(orc.rep_of_temp.copy())
+        log["rot_before"], log["rot_after"], log["xround_before"] = np.array(rb), np.array(rots), np.array(xrs)
+        last, worst, full = _check_ensemble(g, log, orc, sp.ensemble_id, sp.n_replicas, sp.n_beads, T, sp.seed, S,
+                                            1000, n_bins, True, rep_off=int(rep_off[e]), pos_off=int(pos_off[e]))
+        assert last >= 5
+        print(f"ensemble {e} (N={sp.n_beads}, R={sp.n_replicas}): {last} sweeps compared, worst E err / tol "
+              f"{worst:.3f}, full match {full}")

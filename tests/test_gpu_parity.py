@@ -249,7 +249,7 @@ def pt_default_kernel(N):
 
 
 @pytest.mark.parametrize("variant", [0, 2, 3, 6])
-@pytest.mark.parametrize("N", [2048, 8192])
+@pytest.mark.parametrize("N", [2048, 4096, 8192])
 def test_longest_chains(N, variant):
     """Chains beyond the register kernels' 1024 beads, up to the largest N the library takes
     (the warp-per-move kernel's shared memory does not fit 8192 beads, and kernel 6 holds at

@@ -135,11 +135,11 @@ def test_paper_scale_configuration_unlogged(variant):
         print(f"kernel {variant}: {last} sweeps compared, worst E err / tol {worst:.3f}, full match {full}")
 
 
-@pytest.mark.parametrize("N,S", [(300, 20), (1000, 10)])
-def test_long_chain_configuration_unlogged(N, S):
+@pytest.mark.parametrize("N,R,S", [(300, 128, 20), (1000, 128, 10), (4096, 8, 3)])
+def test_long_chain_configuration_unlogged(N, R, S):
     """N = 300 and 1000 x 128 replicas, T 0.2-3.0: the benchmark's kernel (6) on its
-    production path against the oracle."""
-    res = _run(N, 128, S, [1], 6)
+    production path against the oracle; and its longest chains (4096 beads, 8 replicas)."""
+    res = _run(N, R, S, [1], 6)
     last, worst, full = res[0]
     assert last >= min(S, 3)
     print(f"N={N}: {last} sweeps compared, worst E err / tol {worst:.3f}, full match {full}")

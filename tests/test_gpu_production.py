@@ -93,22 +93,24 @@ def _check_ensemble(g, o, orc, e, R, N, T, seed, S, recompute_every, n_bins, ful
     return last, worst, full
 
 
-def _run(N, R, S, seeds, variant, recompute_every=1000, n_bins=4096, tmin=0.2, tmax=3.0, threads=16):
+def _run(N, R, S, seeds, variant, recompute_every=1000, n_bins=4096, tmin=0.2, tmax=3.0, threads=16, xe=1,
+         delta=0.3, lj_bonded=1):
     T = inputs.temperature_ladder(tmin, tmax, R)
     made = [pt.make_params(N, T, sd, ensemble_id=e, init_positions=inputs.random_coil(N, R, sd, e),
-                           n_bins=n_bins, recompute_every=recompute_every) for e, sd in enumerate(seeds)]
-    g = _gpu_unlogged(made, variant, S)
+                           n_bins=n_bins, recompute_every=recompute_every, delta=delta, lj_bonded=lj_bonded)
+            for e, sd in enumerate(seeds)]
+    g = _gpu_unlogged(made, variant, S, xe=xe)
     assert g["kernel"] == variant
     out = []
     for e, sd in enumerate(seeds):
         orc = oracle.OracleEnsemble(inputs.random_coil(N, R, sd, e), T, sd, ensemble_id=e, n_bins=n_bins,
-                                    recompute_every=recompute_every, threads=threads)
+                                    recompute_every=recompute_every, threads=threads, delta=delta, lj_bonded=lj_bonded)
         log = orc.enable_log(S)
         rb, rots, xrs = [], [], []
         for _ in range(S):
             rb.append(orc.rep_of_temp.copy())
             xrs.append(orc.xround)
-            orc.run(1, 1)
+            orc.run(1, xe)
             rots.append(orc.rep_of_temp.copy())
         log["rot_before"], log["rot_after"], log["xround_before"] = np.array(rb), np.array(rots), np.array(xrs)
         out.append(_check_ensemble(g, log, orc, e, R, N, T, sd, S, recompute_every, n_bins, True))
@@ -188,3 +190,17 @@ def test_batched_configuration_unlogged_sampled():
         assert last >= 5
         print(f"ensemble {e} (N={sp.n_beads}, R={sp.n_replicas}): {last} sweeps compared, worst E err / tol "
               f"{worst:.3f}, full match {full}")
+
+
+@pytest.mark.parametrize("variant", [4, 5, 6])
+@pytest.mark.parametrize("delta,lj_bonded,xe", [(0.01, 1, 1), (0.3, 0, 3), (0.01, 0, 2)])
+def test_displacement_convention_and_schedule_unlogged(variant, delta, lj_bonded, xe):
+    """The production path with the paper's displacement (0.01: most moves accepted, many
+    corrections between group moves), LJ between non-bonded beads only, and exchange rounds
+    every 2 or 3 sweeps: N = 60 x 16 replicas, 2 seeds, 40 sweeps against the oracle."""
+    res = _run(60, 16, 40, [3, 4], variant, recompute_every=0, n_bins=512, xe=xe, delta=delta,
+               lj_bonded=lj_bonded)
+    for last, worst, full in res:
+        assert last >= 10
+        print(f"kernel {variant}, delta {delta}, lj_bonded {lj_bonded}, xe {xe}: {last} sweeps compared, "
+              f"worst E err / tol {worst:.3f}, full match {full}")

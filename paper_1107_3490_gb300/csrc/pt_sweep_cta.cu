@@ -46,6 +46,7 @@ constexpr int kG = 16;                      // moves per group (16 or 32): halve
 constexpr int kH = kG / 16;                 // halves; each gives 32 values per thread to reduce
 constexpr int kCxStride = kG + 1;           // padded rows of the correction table
 constexpr int kMB = 2;                      // moves per branch-free block of the row pass
+
 constexpr float kDeltaRow = 4.0e-6f;        // 2e-6 for x plus 32 units of 2^-24 of rounding
 constexpr float kSumInfl = 1.0f + 64.f * 5.9604645e-08f;  // covers the round-to-nearest sums of w+
 // Deferred accurate terms held per CTA: 128 per warp; the list is flushed before a group
@@ -255,9 +256,13 @@ __device__ __forceinline__ long long to_fix(float c, int* err) {
 template <int W>
 __host__ __device__ constexpr int ctl_warps() { return W >= 8 ? 4 : W >= 4 ? 3 : 2; }
 
+// Moves drawn per batch, in units of T: four, two with 16 row warps (shared memory).
+template <int W>
+__host__ __device__ constexpr int batch_of() { return W >= 16 ? 2 : 4; }
+
 template <int W>
 __host__ __device__ constexpr size_t cta_fixed_bytes() {
-    return (size_t)(2 * 32 * W) * sizeof(float4)            // D0, D1
+    return (size_t)(2 * batch_of<W>() * 32 * W) * sizeof(float4)   // D0, D1
            + (size_t)(W + ctl_warps<W>()) * kG * 4 * sizeof(float4)  // per-warp move records
            + (size_t)kG * kCxStride * sizeof(float4)        // corrections
            + (size_t)kG * sizeof(float4)                    // bond terms
@@ -274,7 +279,7 @@ __host__ __device__ constexpr size_t cta_fixed_bytes() {
 // per SM holds a 1000-bead replica.
 template <int U, int W>
 __global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_sweep_cta(State S, int chunk) {
-    constexpr int T = 32 * W, V = U / 2, NC = ctl_warps<W>(), TC = T + 32 * NC;
+    constexpr int T = 32 * W, V = U / 2, NC = ctl_warps<W>(), TC = T + 32 * NC, kBatch = batch_of<W>();
     extern __shared__ float4 smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool ctl = warp >= W;          // a control warp
@@ -297,9 +302,9 @@ __global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_s
 
     constexpr int kPendCta = pend_cap<W>();
     float4* P = smem;                              // [nmax] the chain
-    float4* D0 = P + S.nmax;                       // [T] batch move: bead, displacement
-    float4* D1 = D0 + T;                           // [T] batch move: theta, -, -, run length
-    float4* GMall = D1 + T;                        // [W + NC][kG][4] per-warp group records
+    float4* D0 = P + S.nmax;                       // [kBatch T] batch move: bead, displacement
+    float4* D1 = D0 + kBatch * T;                  // [kBatch T] batch move: theta, -, -, run length
+    float4* GMall = D1 + kBatch * T;               // [W + NC][kG][4] per-warp group records
     float4* CX = GMall + (W + NC) * kG * 4;        // [kG][kCxStride] corrections (value, bound, flags)
     float4* BND = CX + kG * kCxStride;             // [kG] bond terms of the group's moves (value, bound, flags)
     float4* PE = BND + kG;                         // [kPendCta][3] deferred accurate terms
@@ -386,39 +391,39 @@ __global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_s
         const size_t lrow = logging ? (size_t)(s - S.log_s0) * S.log_pstride + rd.pos_off : 0;
         df dsum = {0.f, 0.f};  // accepted values (the control warp's copy is used)
         int nacc = 0;
-        for (int m0 = 0; m0 < N; m0 += T) {
-            // ---- batch: draws of move m0 + tid, and the run of distinct beads from each
-            const int mc = min(T, N - m0);
+        for (int m0 = 0; m0 < N; m0 += kBatch * T) {
+            // ---- batch: draws of moves m0 + j, and the run of distinct beads from each
+            const int mc = min(kBatch * T, N - m0);
             __syncthreads();  // the previous batch's arrays are no longer read
-            if (tid < mc) {
-                const uint32_t m = (uint32_t)(m0 + tid);
+            for (int j = tid; j < mc; j += TC) {
+                const uint32_t m = (uint32_t)(m0 + j);
                 const u4 w4 = philox(u4{2u * m, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
                 const u4 v4 = philox(u4{2u * m + 1u, (uint32_t)s, (uint32_t)rd.r, c3}, k0, k1);
                 const int km = (int)__umulhi(w4.x, (uint32_t)N);
                 const float sx = __fsub_rn(__fmul_rn(2.f, unif24(w4.y)), 1.f);
                 const float sy = __fsub_rn(__fmul_rn(2.f, unif24(w4.z)), 1.f);
                 const float sz = __fsub_rn(__fmul_rn(2.f, unif24(w4.w)), 1.f);
-                D0[tid] = make_float4(__int_as_float(km), sx, sy, sz);
-                D1[tid] = make_float4(__fmul_rn(-logf(unif24(v4.x)), Tf), 0.f, 0.f, 0.f);
+                D0[j] = make_float4(__int_as_float(km), sx, sy, sz);
+                D1[j] = make_float4(__fmul_rn(-logf(unif24(v4.x)), Tf), 0.f, 0.f, 0.f);
             }
             __syncthreads();
-            if (tid < mc) {
+            for (int j0 = tid; j0 < mc; j0 += TC) {
                 int len = 1;
                 if (!logging) {
                     int kb[kG];
 #pragma unroll
-                    for (int j = 0; j < kG; ++j) kb[j] = tid + j < mc ? __float_as_int(D0[tid + j].x) : -1 - j;
+                    for (int j = 0; j < kG; ++j) kb[j] = j0 + j < mc ? __float_as_int(D0[j0 + j].x) : -1 - j;
                     bool stop = false;
 #pragma unroll
                     for (int j = 1; j < kG; ++j) {
-                        bool dup = tid + j >= mc;
+                        bool dup = j0 + j >= mc;
 #pragma unroll
                         for (int l = 0; l < j; ++l) dup |= kb[l] == kb[j];
                         stop |= dup;
                         if (!stop) len = j + 1;
                     }
                 }
-                D1[tid].w = __int_as_float(len);
+                D1[j0].w = __int_as_float(len);
             }
             __syncthreads();
             for (int g0 = 0; g0 < mc;) {

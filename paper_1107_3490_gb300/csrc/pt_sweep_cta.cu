@@ -250,11 +250,12 @@ __device__ __forceinline__ long long to_fix(float c, int* err) {
 
 }  // namespace
 
-// Control warps of a CTA with W row warps: one per SM sub-partition from 8 row warps on; 3
-// with 4 or 5 row warps and 2 with 2 (measured: N = 300 x 128 replicas 105 -> 90 us per
-// sweep with 3 control warps instead of 1; N = 100 x 256 replicas 64 -> 62 us with 2).
+// Control warps of a CTA with W row warps: 4 beside 16 row warps, 3 beside 4 to 8, 2 beside
+// 2 (measured: N = 300 x 128 replicas 105 -> 90 us per sweep with 3 control warps instead of
+// 1; N = 100 x 256 replicas 64 -> 62 us with 2; N = 1000 x 128 300.6 us with 4, 298.9 with 3,
+// 301.0 with 2, 310.1 with 5). Every control warp takes issue slots from the row warps.
 template <int W>
-__host__ __device__ constexpr int ctl_warps() { return W >= 8 ? 4 : W >= 4 ? 3 : 2; }
+__host__ __device__ constexpr int ctl_warps() { return W >= 16 ? 4 : W >= 8 ? 3 : W >= 4 ? 3 : 2; }
 
 // Moves drawn per batch, in units of T: four, two with 16 row warps (shared memory).
 template <int W>
@@ -273,10 +274,9 @@ __host__ __device__ constexpr size_t cta_fixed_bytes() {
 
 // Warps 0..W-1 hold the chain (T = 32 W threads, U beads each) and evaluate the rows; warps
 // W..W+NC-1 are control warps: while the rows run they evaluate the group's bond terms and
-// the corrections of the group pairs that can interact (one control warp per SM
-// sub-partition, so that no row warp shares its issue slots with more than its share), and
-// after the first group barrier control warp 0 takes the decisions. One CTA of 8 + 4 warps
-// per SM holds a 1000-bead replica.
+// the corrections of the group pairs that can interact, and after the first group barrier
+// control warp 0 takes the decisions. One CTA of 8 + 3 warps per SM holds a 1000-bead
+// replica.
 template <int U, int W>
 __global__ void __launch_bounds__(32 * (W + ctl_warps<W>()), W >= 8 ? 1 : 2) k_sweep_cta(State S, int chunk) {
     constexpr int T = 32 * W, V = U / 2, NC = ctl_warps<W>(), TC = T + 32 * NC, kBatch = batch_of<W>();
@@ -808,7 +808,7 @@ int cta_warps(int nmax) {
 // Threads of a CTA: the row warps and the control warps.
 static int cta_threads(int nmax) {
     const int w = cta_warps(nmax);
-    return 32 * (w + (w >= 8 ? 4 : w >= 4 ? 3 : 2));
+    return 32 * (w + (w >= 16 ? 4 : w >= 8 ? 3 : w >= 4 ? 3 : 2));
 }
 
 // The kernel of a shape, as a function pointer (nullptr: no such instantiation).

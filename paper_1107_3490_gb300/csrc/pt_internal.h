@@ -121,6 +121,11 @@ cudaError_t launch_sweep_cta_coop(const State& s, int chunk, cudaStream_t st);
 int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant);
 size_t sweep_smem_bytes(int nmax, int warps, int variant);
 cudaError_t configure_sweep(int nmax, int warps, int variant);  // per context, before any capture
+// Let kernel f use more than the default 48 KB of dynamic shared memory per block when it
+// needs `need` bytes. The attribute is per function and shared by every context of the
+// process, so it is raised to the GPU's opt-in limit, never set to one context's need: a
+// context with shorter chains must not lower it below what another launches with.
+cudaError_t allow_dynamic_smem(const void* f, size_t need);
 cudaError_t launch_sweep(const State& s, int chunk, int warps, int variant, cudaStream_t st);
 cudaError_t launch_exchange(const State& s, cudaStream_t st);
 // Persistent launches (kernels 4 and 5): all sweeps up to each ensemble's target in one

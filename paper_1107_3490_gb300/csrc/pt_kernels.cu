@@ -944,6 +944,16 @@ int sweep_warps_per_block(int nmax, int n_reps, int num_sms, int variant) {
     return w;
 }
 
+cudaError_t allow_dynamic_smem(const void* f, size_t need) {
+    if (need <= 48 * 1024) return cudaSuccess;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (need > (size_t)optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
 cudaError_t configure_sweep(int nmax, int warps, int variant) {
     const size_t smem = sweep_smem_bytes(nmax, warps, variant);
     if (variant == kSweepCta) return configure_sweep_cta(nmax);
@@ -951,25 +961,22 @@ cudaError_t configure_sweep(int nmax, int warps, int variant) {
     if (variant == kSweepGrp) return nmax <= kRegMaxN ? configure_sweep_grp(nmax) : cudaErrorInvalidValue;
     if (smem <= 48 * 1024) return cudaSuccess;
     if (variant == kSweepWpm) {
-        const int a = (int)smem;
         switch (warps) {
-            case 2: return cudaFuncSetAttribute(k_sweep_wpm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
-            case 4: return cudaFuncSetAttribute(k_sweep_wpm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
-            default: return cudaFuncSetAttribute(k_sweep_wpm<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+            case 2: return allow_dynamic_smem((const void*)k_sweep_wpm<2>, smem);
+            case 4: return allow_dynamic_smem((const void*)k_sweep_wpm<4>, smem);
+            default: return allow_dynamic_smem((const void*)k_sweep_wpm<8>, smem);
         }
     }
     if (variant == kSweepTeam) {
-        const int a = (int)smem;
         switch (warps) {
-            case 1: return cudaFuncSetAttribute(k_sweep_team<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
-            case 2: return cudaFuncSetAttribute(k_sweep_team<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
-            case 4: return cudaFuncSetAttribute(k_sweep_team<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
-            default: return cudaFuncSetAttribute(k_sweep_team<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+            case 1: return allow_dynamic_smem((const void*)k_sweep_team<1>, smem);
+            case 2: return allow_dynamic_smem((const void*)k_sweep_team<2>, smem);
+            case 4: return allow_dynamic_smem((const void*)k_sweep_team<4>, smem);
+            default: return allow_dynamic_smem((const void*)k_sweep_team<8>, smem);
         }
     }
-    return variant == kSweepLookahead
-               ? cudaFuncSetAttribute(k_sweep_la, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-               : cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return variant == kSweepLookahead ? allow_dynamic_smem((const void*)k_sweep_la, smem)
+                                      : allow_dynamic_smem((const void*)k_sweep, smem);
 }
 
 cudaError_t launch_sweep(const State& s, int chunk, int warps, int variant, cudaStream_t st) {

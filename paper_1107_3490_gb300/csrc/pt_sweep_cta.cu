@@ -829,7 +829,7 @@ cudaError_t configure_sweep_cta(int nmax) {
     if (nmax > kCtaMaxN) return cudaErrorInvalidValue;
     const size_t smem = cta_smem_bytes(nmax);
     if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(cta_kernel(nmax), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return allow_dynamic_smem(cta_kernel(nmax), smem);
 }
 
 cudaError_t launch_sweep_cta(const State& s, int chunk, cudaStream_t st) {

@@ -589,7 +589,7 @@ template <int W>
 static cudaError_t configure_grp_w(int smem) {
     cudaError_t e = cudaSuccess;
     auto set = [&](auto kern) {
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = allow_dynamic_smem((const void*)kern, (size_t)smem);
     };
     set(k_sweep_grp<1, W>);
     set(k_sweep_grp<2, W>);

@@ -439,7 +439,7 @@ cudaError_t launch_sweep_wl(const State& s, const WorkList& wl, int num_sms, cud
 cudaError_t configure_sweep_wl(int nmax) {
     const size_t smem = reg_smem_bytes(nmax);
     if (smem <= 48 * 1024) return cudaSuccess;
-    auto set = [&](const void* f) { return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); };
+    auto set = [&](const void* f) { return allow_dynamic_smem(f, smem); };
     switch (reg_slots(nmax)) {
         case 16: return set((const void*)k_sweep_wl<16>);
         case 32: return set((const void*)k_sweep_wl<32>);

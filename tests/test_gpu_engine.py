@@ -451,3 +451,29 @@ def test_worklist_wait_gives_up_and_the_context_recovers():
     finally:
         pt.pt_destroy(h)
         pt.pt_destroy(ref)
+
+
+@pytest.mark.parametrize("variant,sizes", [(6, [(248, 16), (173, 16)]), (5, [(1000, 8), (600, 8)])])
+def test_contexts_with_different_chains_share_a_kernel(variant, sizes):
+    """Two contexts whose chains take the same kernel instantiation with different amounts of
+    shared memory above 48 KB: the context with shorter chains, created second, must not lower
+    the first one's shared-memory allowance (which a cooperative launch reports as too many
+    blocks). Both sweep in both launch modes."""
+    hs, keep = [], []
+    try:
+        for k, (N, R) in enumerate(sizes):
+            p, kp = pt.make_params(N, inputs.temperature_ladder(0.2, 3.0, R), 11 + k,
+                                   init_positions=inputs.random_coil(N, R, 11 + k), n_bins=128)
+            keep.append(kp)
+            h = pt.pt_create_ex(p)
+            hs.append(h)
+            pt.pt_set_sweep_kernel(h, variant)
+        for mode in (1, 0):
+            for h in hs:
+                pt.pt_set_launch_mode(h, mode)
+                pt.pt_sweep(h, 3, 1)
+                pt.pt_sync(h)
+                assert np.all(np.isfinite(pt.pt_energies(h)))
+    finally:
+        for h in hs:
+            pt.pt_destroy(h)

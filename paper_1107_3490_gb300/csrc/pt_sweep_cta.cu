@@ -14,6 +14,9 @@
 // corrections between its moves. After a barrier, the first control warp adds the warps'
 // sums, takes the group's decisions and writes the accepted moves into the chain in shared
 // memory; after a second barrier every row thread reloads the slots an acceptance changed.
+// The moves' random numbers are drawn a batch at a time (4 T moves, 2 T with 16 row warps)
+// together with the run of distinct beads from every move, so that up to 1024 beads a group
+// is cut by a batch end at most once per sweep.
 //
 // Bound. A row term is t = x_n (A x_n - B) - x_o (A x_o - B), x = r^-6, computed as
 // (x_n - x_o)(A (x_n + x_o) - B). x carries a relative error of at most 17 units of 2^-24
@@ -46,7 +49,6 @@ constexpr int kG = 16;                      // moves per group (16 or 32): halve
 constexpr int kH = kG / 16;                 // halves; each gives 32 values per thread to reduce
 constexpr int kCxStride = kG + 1;           // padded rows of the correction table
 constexpr int kMB = 2;                      // moves per branch-free block of the row pass
-
 constexpr float kDeltaRow = 4.0e-6f;        // 2e-6 for x plus 32 units of 2^-24 of rounding
 constexpr float kSumInfl = 1.0f + 64.f * 5.9604645e-08f;  // covers the round-to-nearest sums of w+
 // Deferred accurate terms held per CTA: 128 per warp; the list is flushed before a group

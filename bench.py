@@ -39,7 +39,7 @@ KERNEL_NAMES = {0: "k_sweep", 1: "k_sweep_la", 2: "k_sweep_team", 3: "k_sweep_wp
 KERNEL_DESC = {0: "warp per replica", 1: "lookahead groups of 8 moves", 2: "team of warps per replica",
                3: "warp per move of a group", 4: "warp per replica, chain in registers, deferred double-float",
                5: "CTA per replica, one warp per move of a group, chain in registers",
-               6: "CTA per replica, every thread a chain slice and a group of 16 moves in packed FP32x2, control warp"}
+               6: "CTA per replica, every thread a chain slice and a group of 16 moves in packed FP32x2, control warps"}
 UNIT = "updates/s"
 # The plain (one-context) workloads: beads, replicas, ensembles per GPU.
 PLAIN = {

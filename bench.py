@@ -49,7 +49,7 @@ PLAIN = {
 # DRAM bytes read + written per sweep (ncu dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch of the kernel as it stands, divided by the sweeps that launch ran), keyed by
 # (workload, kernel, launch mode); pairs without a current capture report null
-TRAFFIC_BYTES = {("long", "k_sweep_cta", 1): 2671, ("paper-scale", "k_sweep_cta", 1): 2782}
+TRAFFIC_BYTES = {("long", "k_sweep_cta", 1): 2926, ("paper-scale", "k_sweep_cta", 1): 2763}
 
 
 def workload_text(w):
